@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Throughput of the per-frame probe update + change selection + packing on GB300.
+
+Metric: probes updated+packed per second on a 16x16x16 probe volume with 256
+rays per probe (colour 6x6 / visibility 14x14 interiors, FP16 texel state,
+hysteresis 0.97, sharpness 50), FP32 ray inputs (the plain FP32 form).
+One step = one frame: probe_update (weights + blend + guard band + change
+flags) and probe_select_and_pack (selection, index buffers, colour and
+visibility planes), each step replayed as a CUDA graph. Inputs are seeded
+synthetic ray payloads (lognormal radiance, uniform hit distance with 10%
+misses), fresh each frame ("noisy" mode: nearly every probe changes, the
+packing worst case); 8 distinct input frames are cycled, 168 MB in total,
+which is larger than L2, while the volume's own state stays resident as in
+steady-state serving.
+
+`--impl reference` times the FP64 CPU oracle (the only other implementation
+of this path) on the same workload, one frame per step, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NBUF = 8
+METRIC = "probes updated+packed/sec at 16^3 probes x 256 rays (plain FP32 form)"
+UNIT = "probes/s"
+WORKLOAD = "16x16x16 probes, 256 rays/probe, colour 6x6+1, vis 14x14+1, FP16 state, h=0.97, s=50"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="f32,f16,bf16")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def blend_bytes_per_probe(R, op_bytes, nc=6, nv=14, state_bytes=2):
+    """Algorithmic HBM bytes of the blend kernel per probe: ray payload read, interior
+    texels read, full tiles written, last-transmitted codes read, 5 flag bytes written."""
+    Tc, Tv, tc, tv = nc * nc, nv * nv, (nc + 2) ** 2, (nv + 2) ** 2
+    return (4 * R * op_bytes + (3 * Tc + 2 * Tv) * state_bytes + (3 * tc + 2 * tv) * state_bytes
+            + (3 * Tc + 2 * Tv) * 2 + 5)
+
+
+# ------------------------------------------------------------------ our arm
+def make_inputs(spec, seed, nbuf):
+    import torch
+    import pv_workload as wl
+    fs = wl.FrameStream(spec, seed, mode="noisy")
+    bufs = []
+    for f in range(nbuf):
+        rad = wl.to_operand(fs.radiance(f), spec.operand_fmt).cuda()
+        dist = wl.to_operand(fs.dist(f), spec.operand_fmt).cuda()
+        dirs = torch.from_numpy(fs.directions(f)).cuda()
+        bufs.append((rad, dist, dirs))
+    return fs, bufs
+
+
+def time_form(spec, steps, warmup, seed):
+    """Graph-replayed steps with events around the blend kernel; returns timings."""
+    import torch
+    import paper_2103_05875_gb300 as pv
+    fs, bufs = make_inputs(spec, seed, NBUF)
+    vol = pv.ProbeVolume(spec)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    try:
+        ev = lambda: torch.cuda.Event(enable_timing=True, external=True)  # noqa: E731
+        ev()
+        use_graphs = True
+    except TypeError:
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        use_graphs = False
+
+    def step(s, e):
+        rad, dist, dirs = bufs[s % NBUF]
+        e[0].record()
+        pv.probe_update_weights(vol.handle, dirs)
+        e[1].record()
+        pv.probe_update_blend(vol.handle, rad, dist)
+        e[2].record()
+        vol.select_and_pack()
+        e[3].record()
+
+    n = warmup + steps
+    events = [[ev() for _ in range(4)] for _ in range(n)]
+    with torch.cuda.stream(stream):
+        step(0, [torch.cuda.Event(enable_timing=True) for _ in range(4)])   # eager first frame
+    torch.cuda.synchronize()
+    graphs = []
+    if use_graphs:
+        for s in range(n):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                step(s + 1, events[s])
+            graphs.append(g)
+    torch.cuda.synchronize()
+
+    def run(s):
+        if use_graphs:
+            graphs[s].replay()
+        else:
+            step(s + 1, events[s])
+
+    with torch.cuda.stream(stream):
+        for s in range(warmup):
+            run(s)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t0.record()
+        for s in range(warmup, n):
+            run(s)
+        t1.record()
+    torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    blend = [events[s][1].elapsed_time(events[s][2]) for s in range(warmup, n)]
+    weights = [events[s][0].elapsed_time(events[s][1]) for s in range(warmup, n)]
+    pack = [events[s][2].elapsed_time(events[s][3]) for s in range(warmup, n)]
+    fr = vol.select_and_pack(want_host_counts=True)   # extra call: counts of an empty frame
+    res = dict(total_ms=total_ms, blend_ms=statistics.mean(blend), weights_ms=statistics.mean(weights),
+               select_pack_ms=statistics.mean(pack), kernel=vol.kernel, graphs=use_graphs,
+               launches_per_step=1 + 1 + 1 + 2)
+    vol.close()
+    del bufs
+    torch.cuda.empty_cache()
+    return res
+
+
+def time_e2e(spec, steps, seed):
+    """Host buffers through the C ABI: H2D of the frame's rays and D2H of the packed frame."""
+    import numpy as np
+    import torch
+    import paper_2103_05875_gb300 as pv
+    import pv_workload as wl
+    fs = wl.FrameStream(spec, seed, mode="noisy")
+    host = []
+    for f in range(2):
+        rad = wl.to_operand(fs.radiance(f), spec.operand_fmt).pin_memory()
+        dist = wl.to_operand(fs.dist(f), spec.operand_fmt).pin_memory()
+        dirs = torch.from_numpy(fs.directions(f)).pin_memory()
+        host.append((rad, dist, dirs))
+    vol = pv.ProbeVolume(spec)
+    info = vol.info
+    color = torch.empty((3, info.color_height, info.color_width), dtype=torch.int16).pin_memory()
+    vis = torch.empty((3, info.vis_height, info.vis_width), dtype=torch.uint8).pin_memory()
+    dc = torch.empty(vol.P, dtype=torch.int16).pin_memory()
+    dv = torch.empty(vol.P, dtype=torch.int16).pin_memory()
+    counts = np.zeros(2, dtype=np.uint32)
+    stream = torch.cuda.current_stream()
+    bi = sum(t.numel() * t.element_size() for t in host[0])
+    bo_fixed = color.numel() * 2 + vis.numel() + 8
+
+    def one(s):
+        rad, dist, dirs = host[s % 2]
+        pv.probe_update_host(vol.handle, rad, dist, dirs)
+        vol.select_and_pack()
+        pv.probe_frame_download(vol.handle, color, vis, dc, dv, counts)
+        return int(counts[0] + counts[1]) * 2
+
+    for s in range(3):
+        one(s)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    idx_bytes = 0
+    t0.record(stream)
+    for s in range(steps):
+        idx_bytes += one(s)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    vol.close()
+    return {"value": vol.P * steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": int(bo_fixed + idx_bytes / steps), "ms_per_step": ms / steps}
+
+
+def cpu_baseline(spec, seed, budget_s=12.0, max_frames=40):
+    """The FP64 oracle as it stands, on a bounded number of frames of the same workload."""
+    import numpy as np
+    import pv_workload as wl
+    from oracle import OracleVolume
+    fs = wl.FrameStream(spec, seed, mode="noisy")
+    ov = OracleVolume(spec)
+    frames, t_used = 0, 0.0
+    while frames < max_frames and t_used < budget_s:
+        L, D, d = (fs.radiance(frames).astype(np.float64), fs.dist(frames).astype(np.float64),
+                   fs.directions(frames).astype(np.float64))
+        t = time.perf_counter()
+        ov.step(L, D, d)
+        t_used += time.perf_counter() - t
+        frames += 1
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        pass
+    return {"value": spec.probes * frames / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{frames} frames of the 16^3 x 256-ray noisy workload, FP64 numpy "
+                      f"(matmul on up to {cores} BLAS threads, the rest on one core), {t_used:.1f} s"}
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import pv_workload as wl
+    from oracle import OracleVolume
+    spec = wl.config2()
+    fs = wl.FrameStream(spec, wl.config_seed(2), mode="noisy")
+    ov = OracleVolume(spec)
+    inputs = [(fs.radiance(f).astype(np.float64), fs.dist(f).astype(np.float64),
+               fs.directions(f).astype(np.float64)) for f in range(2)]
+    for s in range(args.warmup):
+        ov.step(*inputs[s % 2])
+    t = time.perf_counter()
+    for s in range(args.steps):
+        ov.step(*inputs[s % 2])
+    dt = time.perf_counter() - t
+    value = spec.probes * args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "mode": "noisy"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed frames after {args.warmup} warm-up frames"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import pv_workload as wl
+    torch.cuda.set_device(local)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    forms = [f for f in args.forms.split(",") if f]
+    seed = wl.config_seed(2) + 1000 * rank
+    results = {}
+    clocks = Clocks(local)
+    barrier(ws)
+    clocks.start()
+    for form in forms:
+        results[form] = time_form(wl.config2(operand_fmt=form), args.steps, args.warmup, seed)
+    clk = clocks.stop()
+    head = results[forms[0]]
+    t_max = max_over_ranks(head["total_ms"], ws)
+    P = 4096
+    value = P * args.steps * ws / (t_max / 1e3)
+    op_bytes = 4 if forms[0] == "f32" else 2
+    bpp = blend_bytes_per_probe(256, op_bytes)
+    alg = bpp * P + (36 + 196) * 256 * 4
+    achieved = alg / (head["blend_ms"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": forms[0], "mode": "noisy (fresh rays every frame)",
+                   "l2": f"inputs larger than L2: {NBUF} distinct frames cycled",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single volume",
+                   "graphs": head["graphs"], "blend_kernel": head["kernel"]},
+        "gpu_launches": head["launches_per_step"] * args.steps,
+        "breakdown_ms_per_step": {"weights": head["weights_ms"], "blend": head["blend_ms"],
+                                  "select_pack": head["select_pack_ms"]},
+        "forms": {f: {"value": P * args.steps / (r["total_ms"] / 1e3), "ms_per_step": r["total_ms"] / args.steps,
+                      "blend_ms": r["blend_ms"], "kernel": r["kernel"]} for f, r in results.items()},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "kernel": "blend",
+                     "peak_source": peak_src, "algorithmic_bytes_per_launch": alg},
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_e2e:
+        line["e2e"] = time_e2e(wl.config2(operand_fmt=forms[0]), max(10, args.steps // 2), seed)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl.config2(), seed)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * probe_stream.h -- C ABI of the GB300 probe-streaming hot path.
+ *
+ * The library implements the server side of "A Distributed, Decoupled System
+ * for Losslessly Streaming Dynamic Light Probes to Thin Clients" (arXiv
+ * 2103.05875) for one GPU: each frame it blends traced rays into the
+ * octahedral irradiance and visibility texels of every probe of a volume
+ * (Section 3.2), refills the one-texel guard bands (Section 3.4, Light Probe
+ * Repacking), selects the probes whose transmitted codes changed since they
+ * were last sent (Section 3.4, Light Probe Change Thresholding), and packs the
+ * selected interiors into the lossless-video plane layouts (Section 3.3) with
+ * a delta-coded 16-bit probe index buffer (Section 3.4, Light Probe Update
+ * Textures). The HEVC encode itself is not part of the library: it hands back
+ * packed frames.
+ *
+ * Conventions for every entry point:
+ *  - Errors are returned as pv_status; nothing throws across the ABI.
+ *    pv_last_error() gives a human-readable message for the calling thread.
+ *  - "device pointer" means memory of the volume's CUDA device; "host or
+ *    device" means any pointer CUDA's unified addressing resolves (pageable
+ *    host, pinned host or device).
+ *  - Streams are passed as an opaque cudaStream_t (void*); NULL is the legacy
+ *    default stream. Asynchronous calls only enqueue work on that stream; the
+ *    caller keeps inputs alive and unmodified until the stream has passed the
+ *    call.
+ *  - Volumes own all of their state and output buffers. A volume may be used
+ *    from one host thread at a time.
+ *  - Array layouts (row-major, P = nx*ny*nz probes, R rays per probe,
+ *    probe id p = x + nx*(y + ny*z), n_c / n_v interior sizes, tiles of
+ *    (n+2)x(n+2) texels):
+ *      radiance      [3][P][R]            operand format (R, G, B planes)
+ *      dist          [P][R]               operand format
+ *      dirs          [R][3]               float32 unit ray directions
+ *      colour tiles  [3][P][n_c+2][n_c+2] state format
+ *      vis tiles     [2][P][n_v+2][n_v+2] state format (mean d, mean d^2)
+ *      last codes    colour [3][P][n_c*n_c], vis [2][P][n_v*n_v] uint16;
+ *                    0xFFFF marks a probe never sent
+ */
+#ifndef PROBE_STREAM_H
+#define PROBE_STREAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pv_status {
+  PV_OK = 0,
+  PV_PENDING = 1,        /* pv_poll: the ticket's tick has not completed yet */
+  PV_ERR_INVALID = -1,   /* bad argument, shape or descriptor field */
+  PV_ERR_OOM = -2,       /* device allocation failed or memory budget exceeded */
+  PV_ERR_CUDA = -3,      /* a CUDA call or kernel launch failed */
+  PV_ERR_BUSY = -4,      /* no free slot in the server right now */
+  PV_ERR_TIMEOUT = -5,   /* a bounded wait gave up */
+  PV_ERR_RANGE = -6,     /* a size limit was exceeded (e.g. > 65536 probes) */
+  PV_ERR_UNSUPPORTED = -7 /* valid request the chosen kernel cannot serve */
+} pv_status;
+
+enum { PV_FMT_F32 = 0, PV_FMT_F16 = 1, PV_FMT_BF16 = 2 };
+enum { PV_CODE_UF10 = 0, PV_CODE_UNORM10 = 1 };
+enum { PV_KERNEL_AUTO = 0, PV_KERNEL_SIMT = 1, PV_KERNEL_TCGEN05 = 2 };
+
+/* Limits checked by probe_volume_create. */
+#define PV_MAX_PROBES 65536   /* probe ids must fit the 2-byte index buffer (Section 3.4) */
+#define PV_MAX_RAYS 1024
+#define PV_MAX_INTERIOR 16    /* n_c, n_v <= 16: at most 256 texels per tile */
+
+/*
+ * Volume descriptor. The blend (Section 3.2, after DDGI) of texel t with
+ * direction n_t over rays r with directions d_r:
+ *   colour:     W = max(0, n_t . d_r)
+ *   visibility: W = max(0, n_t . d_r)^sharpness, applied to d and d^2
+ *   m = sum_r W x_r / sum_r W;  new = h*old + (1-h)*m  (a texel whose weight
+ *   sum is zero keeps its value), then one rounding to state_fmt.
+ */
+typedef struct pv_desc {
+  int32_t nx, ny, nz;           /* probe grid; P = nx*ny*nz <= PV_MAX_PROBES */
+  int32_t rays_per_probe;       /* R, 1..PV_MAX_RAYS (paper: 256, Section 4) */
+  int32_t color_interior;       /* n_c (paper 8, i.e. 10x10 tiles; default 6) */
+  int32_t vis_interior;         /* n_v (paper 16, i.e. 18x18 tiles; default 14) */
+  float hysteresis;             /* h in [0, 1) */
+  float sharpness;              /* visibility cosine exponent (> 0) */
+  int32_t state_fmt;            /* PV_FMT_F32 or PV_FMT_F16 */
+  int32_t operand_fmt;          /* format of radiance/dist inputs and of the contraction */
+  int32_t color_code;           /* PV_CODE_UF10 (default) or PV_CODE_UNORM10 */
+  int32_t color_lsb;            /* 0: 16-bit sample = code << 6 (default); 1: code in low bits */
+  int32_t first_frame_no_hysteresis; /* 1: the first update uses h = 0 */
+  int32_t kernel;               /* PV_KERNEL_* choice of the blend kernel */
+} pv_desc;
+
+typedef struct pv_volume pv_volume;
+
+/* Sizes of a volume's buffers and output frames (filled by probe_volume_info). */
+typedef struct pv_volume_info {
+  int32_t probes, rays, color_tile, vis_tile;
+  int32_t blocks_w, blocks_h;                   /* update-texture block grid: nx*ny by nz */
+  int32_t color_width, color_height, color_pitch_bytes; /* per colour plane (uint16 samples) */
+  int32_t vis_width, vis_height, vis_pitch_bytes;       /* per visibility plane (uint8 samples) */
+  int32_t kernel;                               /* blend kernel actually used */
+  int32_t state_bytes_per_texel;
+  uint64_t device_bytes;                        /* device memory the volume holds */
+} pv_volume_info;
+
+/*
+ * One packed update (Sections 3.3-3.4). All pointers are device pointers owned
+ * by the volume and stay valid until the next probe_select_and_pack on it.
+ *  color_planes  3 planes (Y=R, U=G, V=B), each color_height rows of
+ *                color_pitch_bytes; sample = 10-bit code << 6 (or << 0).
+ *  vis_planes    3 planes (Y, U, V), each vis_height rows of vis_pitch_bytes;
+ *                the first vis_width bytes of a row are the widened byte stream
+ *                of x = blocks_w*n_v RG16F texels (x' = ceil(4x/3)); the rest
+ *                of the pitch is zero.
+ *  index_*       probe ids of the selected probes in slot order (ascending).
+ *  delta_*       the same ids delta-encoded: d0 = id0, dk = id_k - id_(k-1).
+ *  count_*_dev   device uint32 counts; count_c/count_v are host copies when
+ *                requested (-1 otherwise).
+ * Slot k of either texture holds its probe's interior at block
+ * (k / blocks_w, k % blocks_w); unused slots are zero.
+ */
+typedef struct pv_frame {
+  uint16_t* color_planes;
+  uint8_t* vis_planes;
+  uint16_t* index_c;
+  uint16_t* index_v;
+  uint16_t* delta_c;
+  uint16_t* delta_v;
+  uint32_t* count_c_dev;
+  uint32_t* count_v_dev;
+  int64_t count_c;
+  int64_t count_v;
+  uint64_t frame;                               /* number of updates so far */
+} pv_frame;
+
+/* ----------------------------------------------------------------- basics */
+const char* pv_status_string(pv_status s);
+/* Message of the last failed call on this host thread ("" if none). */
+const char* pv_last_error(void);
+/* Library version string. */
+const char* pv_version(void);
+
+/*
+ * Ray directions helper for callers that generate or trace rays: a spherical
+ * Fibonacci set of `rays` points rotated by a uniform random rotation
+ * (Shoemake 1992) drawn from SplitMix64 keyed by (seed, volume, frame).
+ * The paper leaves the direction set to DDGI; the blend takes directions as an
+ * input, so any set may be passed to probe_update. out_dirs: host [rays][3].
+ */
+pv_status pv_ray_directions(uint64_t seed, uint64_t volume, uint64_t frame, int32_t rays,
+                            float* out_dirs);
+
+/* Device bytes probe_volume_create would allocate for desc (for admission). */
+pv_status probe_volume_bytes(const pv_desc* desc, uint64_t* out_bytes);
+
+/*
+ * Create a volume on the current CUDA device: tiles zero, every probe
+ * "never sent", frame counter 0. Errors: PV_ERR_INVALID (bad field),
+ * PV_ERR_RANGE (limits above), PV_ERR_OOM, PV_ERR_UNSUPPORTED (kernel choice
+ * not available for this shape), PV_ERR_CUDA.
+ */
+pv_status probe_volume_create(const pv_desc* desc, pv_volume** out);
+pv_status probe_volume_destroy(pv_volume* vol);
+pv_status probe_volume_info(const pv_volume* vol, pv_volume_info* out);
+
+/*
+ * Blend one frame of traced rays into the volume (Section 3.2) and refill the
+ * guard bands (Section 3.4); also compares the new transmitted codes with the
+ * last-transmitted ones and records which probes changed (Section 3.4).
+ * radiance [3][P][R], dist [P][R] in operand_fmt; dirs [R][3] float32; all
+ * device pointers. Asynchronous on `stream`; advances the frame counter.
+ * Errors: PV_ERR_INVALID (NULL pointer), PV_ERR_CUDA (launch failure).
+ */
+pv_status probe_update(pv_volume* vol, const void* radiance, const void* dist,
+                       const float* dirs, void* stream);
+
+/*
+ * The two halves of probe_update, for callers that time or schedule them
+ * separately: probe_update_weights computes this frame's blend weights and
+ * weight sums from dirs [R][3] (device float32) and advances the frame
+ * counter (K0); probe_update_blend blends radiance and dist with those weights
+ * (K1: blend, hysteresis, guard band, changed flags). probe_update(v, r, d, q, s)
+ * is exactly probe_update_weights(v, q, s) followed by probe_update_blend(v, r, d, s).
+ */
+pv_status probe_update_weights(pv_volume* vol, const float* dirs, void* stream);
+pv_status probe_update_blend(pv_volume* vol, const void* radiance, const void* dist, void* stream);
+
+/*
+ * Select the changed probes and pack them (Sections 3.3-3.4): builds the
+ * index buffers, writes the colour and visibility planes, and writes the sent
+ * codes to the last-transmitted textures. Asynchronous unless
+ * want_host_counts != 0, in which case the call waits for the stream and
+ * fills out->count_c / count_v. out: host pv_frame.
+ */
+pv_status probe_select_and_pack(pv_volume* vol, pv_frame* out, int32_t want_host_counts,
+                                void* stream);
+
+/*
+ * End-to-end variants with host buffers: probe_update_host copies radiance,
+ * dist and dirs (host or device, layouts as above) into volume-owned device
+ * staging with cudaMemcpyAsync, then runs probe_update. probe_frame_download
+ * copies the last packed frame to host buffers (any may be NULL to skip):
+ * color [3][color_height][color_width] uint16, vis [3][vis_height][vis_width]
+ * uint8, index_c/index_v [P] uint16 (only the first count entries written),
+ * counts[2] (colour, visibility). It synchronises the stream.
+ */
+pv_status probe_update_host(pv_volume* vol, const void* radiance, const void* dist,
+                            const float* dirs, void* stream);
+pv_status probe_frame_download(pv_volume* vol, uint16_t* color, uint8_t* vis,
+                               uint16_t* delta_c, uint16_t* delta_v, uint32_t* counts,
+                               void* stream);
+
+/*
+ * Checkpoint / resume and test injection. Buffers are host or device, layouts
+ * as above (tiles in state_fmt). import also recomputes the changed-probe
+ * flags against the imported last codes, so a following
+ * probe_select_and_pack selects exactly what the imported state implies.
+ * Both synchronise the stream. frame: number of updates so far.
+ */
+pv_status probe_volume_export_state(pv_volume* vol, void* tiles_c, void* tiles_v,
+                                    uint16_t* last_c, uint16_t* last_v, uint64_t* frame,
+                                    void* stream);
+pv_status probe_volume_import_state(pv_volume* vol, const void* tiles_c, const void* tiles_v,
+                                    const uint16_t* last_c, const uint16_t* last_v,
+                                    uint64_t frame, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROBE_STREAM_H */

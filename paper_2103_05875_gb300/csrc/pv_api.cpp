@@ -1,0 +1,449 @@
+// Host side of the C ABI declared in include/probe_stream.h: descriptor
+// validation, one device allocation per volume carved into its buffers, and
+// the launch sequences of probe_update (K0 weights, K1 blend) and
+// probe_select_and_pack (K2 select, K3/K4 pack).
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "pv_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+pv_status cuda_fail(cudaError_t e, const char* what) {
+  return pv_set_error(PV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Buffer sizes of a volume, computed from its descriptor alone.
+struct Layout {
+  int P, R, nc, nv, tc, tv, Tc, Tv, bw, bh;
+  int cwidth, cheight, cpitch, vwidth, vheight, vpitch;
+  int tc_pad, tv_pad, r_pad;
+  int sb, ob;
+  size_t off_state_c, off_state_v, off_last_c, off_last_v, off_flags, off_wrt, off_sums, off_wop,
+      off_hy, off_frame, off_idx_c, off_idx_v, off_delta_c, off_delta_v, off_counts, off_planes_c,
+      off_planes_v, total;
+};
+
+pv_status validate(const pv_desc* d) {
+  if (!d) return pv_set_error(PV_ERR_INVALID, "descriptor is NULL");
+  if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0)
+    return pv_set_error(PV_ERR_INVALID, "probe grid %dx%dx%d must be positive", d->nx, d->ny, d->nz);
+  const long long P = (long long)d->nx * d->ny * d->nz;
+  if (P > PV_MAX_PROBES)
+    return pv_set_error(PV_ERR_RANGE, "%lld probes exceed the 2-byte index buffer limit %d", P,
+                        PV_MAX_PROBES);
+  if (d->rays_per_probe <= 0 || d->rays_per_probe > PV_MAX_RAYS)
+    return pv_set_error(PV_ERR_RANGE, "rays_per_probe %d outside 1..%d", d->rays_per_probe,
+                        PV_MAX_RAYS);
+  if (d->color_interior <= 0 || d->color_interior > PV_MAX_INTERIOR || d->vis_interior <= 0 ||
+      d->vis_interior > PV_MAX_INTERIOR)
+    return pv_set_error(PV_ERR_RANGE, "tile interiors %d/%d outside 1..%d", d->color_interior,
+                        d->vis_interior, PV_MAX_INTERIOR);
+  if (!(d->hysteresis >= 0.0f && d->hysteresis < 1.0f))
+    return pv_set_error(PV_ERR_INVALID, "hysteresis %g outside [0, 1)", (double)d->hysteresis);
+  if (!(d->sharpness > 0.0f && d->sharpness < 1e4f))
+    return pv_set_error(PV_ERR_INVALID, "sharpness %g must be positive", (double)d->sharpness);
+  if (d->state_fmt != PV_FMT_F32 && d->state_fmt != PV_FMT_F16)
+    return pv_set_error(PV_ERR_INVALID, "state_fmt must be PV_FMT_F32 or PV_FMT_F16");
+  if (d->operand_fmt != PV_FMT_F32 && d->operand_fmt != PV_FMT_F16 && d->operand_fmt != PV_FMT_BF16)
+    return pv_set_error(PV_ERR_INVALID, "operand_fmt must be F32, F16 or BF16");
+  if (d->color_code != PV_CODE_UF10 && d->color_code != PV_CODE_UNORM10)
+    return pv_set_error(PV_ERR_INVALID, "color_code must be UF10 or UNORM10");
+  if (d->kernel != PV_KERNEL_AUTO && d->kernel != PV_KERNEL_SIMT && d->kernel != PV_KERNEL_TCGEN05)
+    return pv_set_error(PV_ERR_INVALID, "kernel must be AUTO, SIMT or TCGEN05");
+  return PV_OK;
+}
+
+Layout layout_of(const pv_desc* d) {
+  Layout L{};
+  L.P = d->nx * d->ny * d->nz;
+  L.R = d->rays_per_probe;
+  L.nc = d->color_interior;
+  L.nv = d->vis_interior;
+  L.tc = L.nc + 2;
+  L.tv = L.nv + 2;
+  L.Tc = L.nc * L.nc;
+  L.Tv = L.nv * L.nv;
+  L.bw = d->nx * d->ny;
+  L.bh = d->nz;
+  L.cwidth = L.bw * L.nc;
+  L.cheight = L.bh * L.nc;
+  L.cpitch = (int)round_up((size_t)L.cwidth * 2, 16);
+  const int W = L.bw * L.nv;
+  L.vwidth = (4 * W + 2) / 3;
+  L.vheight = L.bh * L.nv;
+  L.vpitch = (int)round_up((size_t)4 * ((W + 2) / 3), 16);
+  L.tc_pad = (int)round_up((size_t)L.Tc, 16);
+  L.tv_pad = (int)round_up((size_t)L.Tv, 16);
+  L.r_pad = (int)round_up((size_t)L.R, 64);
+  L.sb = d->state_fmt == PV_FMT_F16 ? 2 : 4;
+  L.ob = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = round_up(off + bytes, 256);
+    return at;
+  };
+  L.off_state_c = take((size_t)3 * L.P * L.tc * L.tc * L.sb);
+  L.off_state_v = take((size_t)2 * L.P * L.tv * L.tv * L.sb);
+  L.off_last_c = take((size_t)3 * L.P * L.Tc * 2);
+  L.off_last_v = take((size_t)2 * L.P * L.Tv * 2);
+  L.off_flags = take((size_t)5 * L.P);
+  L.off_wrt = take((size_t)L.R * (L.Tc + L.Tv) * 4);
+  L.off_sums = take((size_t)(L.Tc + L.Tv) * 4);
+  L.off_wop = take((size_t)(L.tc_pad + L.tv_pad) * L.r_pad * (d->operand_fmt == PV_FMT_F32 ? 8 : 2));
+  L.off_hy = take(16);
+  L.off_frame = take(16);
+  L.off_idx_c = take((size_t)L.P * 2);
+  L.off_idx_v = take((size_t)L.P * 2);
+  L.off_delta_c = take((size_t)L.P * 2);
+  L.off_delta_v = take((size_t)L.P * 2);
+  L.off_counts = take(16);
+  L.off_planes_c = take((size_t)3 * L.cheight * L.cpitch);
+  L.off_planes_v = take((size_t)3 * L.vheight * L.vpitch);
+  L.total = off;
+  return L;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+pv_status pv_set_error(pv_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+extern "C" {
+
+const char* pv_status_string(pv_status s) {
+  switch (s) {
+    case PV_OK: return "PV_OK";
+    case PV_PENDING: return "PV_PENDING";
+    case PV_ERR_INVALID: return "PV_ERR_INVALID";
+    case PV_ERR_OOM: return "PV_ERR_OOM";
+    case PV_ERR_CUDA: return "PV_ERR_CUDA";
+    case PV_ERR_BUSY: return "PV_ERR_BUSY";
+    case PV_ERR_TIMEOUT: return "PV_ERR_TIMEOUT";
+    case PV_ERR_RANGE: return "PV_ERR_RANGE";
+    case PV_ERR_UNSUPPORTED: return "PV_ERR_UNSUPPORTED";
+  }
+  return "PV_UNKNOWN";
+}
+
+const char* pv_last_error(void) { return g_last_error.c_str(); }
+
+const char* pv_version(void) { return "probe-stream-gb300 0.1 (sm_103a)"; }
+
+pv_status probe_volume_bytes(const pv_desc* d, uint64_t* out) {
+  pv_status s = validate(d);
+  if (s != PV_OK) return s;
+  if (!out) return pv_set_error(PV_ERR_INVALID, "out is NULL");
+  *out = layout_of(d).total;
+  return PV_OK;
+}
+
+pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
+  if (!out) return pv_set_error(PV_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  pv_status s = validate(d);
+  if (s != PV_OK) return s;
+  const char* why = nullptr;
+  const bool tc_ok = pv_tc_supported(d, &why);
+  int kernel = d->kernel;
+  if (kernel == PV_KERNEL_TCGEN05 && !tc_ok)
+    return pv_set_error(PV_ERR_UNSUPPORTED, "tcgen05 blend unavailable: %s", why ? why : "?");
+  if (kernel == PV_KERNEL_AUTO) kernel = tc_ok ? PV_KERNEL_TCGEN05 : PV_KERNEL_SIMT;
+
+  const Layout L = layout_of(d);
+  pv_volume* v = (pv_volume*)calloc(1, sizeof(pv_volume));
+  if (!v) return pv_set_error(PV_ERR_OOM, "host allocation failed");
+  v->d = *d;
+  v->kernel = kernel;
+  cudaGetDevice(&v->device);
+  cudaError_t e = cudaMalloc((void**)&v->base, L.total);
+  if (e != cudaSuccess) {
+    free(v);
+    cudaGetLastError();
+    return pv_set_error(PV_ERR_OOM, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+  }
+  v->bytes = L.total;
+  e = cudaMallocHost((void**)&v->host_counts, 4 * sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    cudaFree(v->base);
+    free(v);
+    return pv_set_error(PV_ERR_OOM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+  }
+  v->state_bytes = L.sb;
+  v->op_bytes = L.ob;
+  v->cwidth = L.cwidth;
+  pv_dev& k = v->k;
+  k.P = L.P; k.R = L.R; k.nc = L.nc; k.nv = L.nv; k.tc = L.tc; k.tv = L.tv; k.Tc = L.Tc; k.Tv = L.Tv;
+  k.bw = L.bw; k.bh = L.bh;
+  k.cpitch = L.cpitch; k.ch = L.cheight;
+  k.vpitch = L.vpitch; k.vh = L.vheight; k.vwidth = L.vwidth;
+  k.state_fmt = d->state_fmt; k.operand_fmt = d->operand_fmt; k.color_code = d->color_code;
+  k.color_shift = d->color_lsb ? 0 : 6;
+  k.h = d->hysteresis; k.sharpness = d->sharpness;
+  k.first_frame_no_hysteresis = d->first_frame_no_hysteresis ? 1 : 0;
+  char* b = v->base;
+  k.state_c = b + L.off_state_c;
+  k.state_v = b + L.off_state_v;
+  k.last_c = (uint16_t*)(b + L.off_last_c);
+  k.last_v = (uint16_t*)(b + L.off_last_v);
+  k.flags = (uint8_t*)(b + L.off_flags);
+  k.w_rt = (float*)(b + L.off_wrt);
+  k.sums = (float*)(b + L.off_sums);
+  k.w_op = b + L.off_wop;
+  k.hy = (float*)(b + L.off_hy);
+  k.frame = (unsigned long long*)(b + L.off_frame);
+  k.idx_c = (uint16_t*)(b + L.off_idx_c);
+  k.idx_v = (uint16_t*)(b + L.off_idx_v);
+  k.delta_c = (uint16_t*)(b + L.off_delta_c);
+  k.delta_v = (uint16_t*)(b + L.off_delta_v);
+  k.counts = (uint32_t*)(b + L.off_counts);
+  k.planes_c = (uint16_t*)(b + L.off_planes_c);
+  k.planes_v = (uint8_t*)(b + L.off_planes_v);
+  k.tc_pad = L.tc_pad; k.tv_pad = L.tv_pad; k.r_pad = L.r_pad;
+
+  // zero everything, then mark every probe "never sent"
+  e = cudaMemset(v->base, 0, L.total);
+  if (e == cudaSuccess) e = cudaMemset(k.last_c, 0xFF, (size_t)3 * L.P * L.Tc * 2);
+  if (e == cudaSuccess) e = cudaMemset(k.last_v, 0xFF, (size_t)2 * L.P * L.Tv * 2);
+  if (e == cudaSuccess) e = pv_simt_prepare();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && kernel == PV_KERNEL_TCGEN05) e = pv_tc_plan_create(v);
+  if (e != cudaSuccess) {
+    pv_tc_plan_destroy(v);
+    cudaFreeHost(v->host_counts);
+    cudaFree(v->base);
+    free(v);
+    return cuda_fail(e, "probe_volume_create");
+  }
+  *out = v;
+  return PV_OK;
+}
+
+pv_status probe_volume_destroy(pv_volume* v) {
+  if (!v) return PV_OK;
+  DeviceGuard g(v->device);
+  pv_tc_plan_destroy(v);
+  cudaFree(v->stage_rad);
+  cudaFree(v->stage_dist);
+  cudaFree(v->stage_dirs);
+  cudaFreeHost(v->host_counts);
+  cudaFree(v->base);
+  free(v);
+  return PV_OK;
+}
+
+pv_status probe_volume_info(const pv_volume* v, pv_volume_info* o) {
+  if (!v || !o) return pv_set_error(PV_ERR_INVALID, "NULL argument");
+  const Layout L = layout_of(&v->d);
+  o->probes = L.P;
+  o->rays = L.R;
+  o->color_tile = L.tc;
+  o->vis_tile = L.tv;
+  o->blocks_w = L.bw;
+  o->blocks_h = L.bh;
+  o->color_width = L.cwidth;
+  o->color_height = L.cheight;
+  o->color_pitch_bytes = L.cpitch;
+  o->vis_width = L.vwidth;
+  o->vis_height = L.vheight;
+  o->vis_pitch_bytes = L.vpitch;
+  o->kernel = v->kernel;
+  o->state_bytes_per_texel = L.sb;
+  o->device_bytes = v->bytes;
+  return PV_OK;
+}
+
+pv_status probe_update_weights(pv_volume* v, const float* dirs, void* stream) {
+  if (!v || !dirs) return pv_set_error(PV_ERR_INVALID, "probe_update_weights: NULL argument");
+  DeviceGuard g(v->device);
+  const bool tc = v->kernel == PV_KERNEL_TCGEN05;
+  cudaError_t e = pv_launch_weights(v->k, dirs, tc ? 0 : 1, tc ? 1 : 0, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "weights kernel");
+  v->frame += 1;
+  return PV_OK;
+}
+
+pv_status probe_update_blend(pv_volume* v, const void* rad, const void* dist, void* stream) {
+  if (!v || !rad || !dist) return pv_set_error(PV_ERR_INVALID, "probe_update_blend: NULL argument");
+  DeviceGuard g(v->device);
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = v->kernel == PV_KERNEL_TCGEN05 ? pv_launch_blend_tc(v, rad, dist, st)
+                                                  : pv_launch_blend_simt(v->k, rad, dist, st);
+  if (e != cudaSuccess) return cuda_fail(e, "blend kernel");
+  return PV_OK;
+}
+
+pv_status probe_update(pv_volume* v, const void* rad, const void* dist, const float* dirs,
+                       void* stream) {
+  if (!v || !rad || !dist || !dirs)
+    return pv_set_error(PV_ERR_INVALID, "probe_update: NULL argument");
+  pv_status s = probe_update_weights(v, dirs, stream);
+  if (s != PV_OK) return s;
+  return probe_update_blend(v, rad, dist, stream);
+}
+
+pv_status probe_select_and_pack(pv_volume* v, pv_frame* out, int32_t want_host_counts, void* stream) {
+  if (!v || !out) return pv_set_error(PV_ERR_INVALID, "probe_select_and_pack: NULL argument");
+  DeviceGuard g(v->device);
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = pv_launch_select(v->k, st);
+  if (e == cudaSuccess) e = pv_launch_pack(v->k, st);
+  if (e != cudaSuccess) return cuda_fail(e, "select/pack kernels");
+  out->color_planes = v->k.planes_c;
+  out->vis_planes = v->k.planes_v;
+  out->index_c = v->k.idx_c;
+  out->index_v = v->k.idx_v;
+  out->delta_c = v->k.delta_c;
+  out->delta_v = v->k.delta_v;
+  out->count_c_dev = v->k.counts;
+  out->count_v_dev = v->k.counts + 1;
+  out->count_c = -1;
+  out->count_v = -1;
+  out->frame = v->frame;
+  if (want_host_counts) {
+    e = cudaMemcpyAsync(v->host_counts, v->k.counts, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "count readback");
+    out->count_c = v->host_counts[0];
+    out->count_v = v->host_counts[1];
+  }
+  return PV_OK;
+}
+
+pv_status probe_update_host(pv_volume* v, const void* rad, const void* dist, const float* dirs,
+                            void* stream) {
+  if (!v || !rad || !dist || !dirs)
+    return pv_set_error(PV_ERR_INVALID, "probe_update_host: NULL argument");
+  DeviceGuard g(v->device);
+  const size_t nr = (size_t)3 * v->k.P * v->k.R * v->op_bytes;
+  const size_t nd = (size_t)v->k.P * v->k.R * v->op_bytes;
+  const size_t nq = (size_t)3 * v->k.R * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  if (!v->stage_rad) {
+    e = cudaMalloc(&v->stage_rad, nr);
+    if (e == cudaSuccess) e = cudaMalloc(&v->stage_dist, nd);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v->stage_dirs, nq);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return pv_set_error(PV_ERR_OOM, "staging allocation failed: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaStream_t st = as_stream(stream);
+  e = cudaMemcpyAsync(v->stage_rad, rad, nr, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v->stage_dist, dist, nd, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v->stage_dirs, dirs, nq, cudaMemcpyDefault, st);
+  if (e != cudaSuccess) return cuda_fail(e, "input upload");
+  return probe_update(v, v->stage_rad, v->stage_dist, v->stage_dirs, stream);
+}
+
+pv_status probe_frame_download(pv_volume* v, uint16_t* color, uint8_t* vis, uint16_t* delta_c,
+                               uint16_t* delta_v, uint32_t* counts, void* stream) {
+  if (!v) return pv_set_error(PV_ERR_INVALID, "probe_frame_download: NULL volume");
+  DeviceGuard g(v->device);
+  cudaStream_t st = as_stream(stream);
+  const pv_dev& k = v->k;
+  cudaError_t e = cudaMemcpyAsync(v->host_counts, k.counts, 2 * sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && color)
+    e = cudaMemcpy2DAsync(color, (size_t)v->cwidth * 2, k.planes_c, k.cpitch, (size_t)v->cwidth * 2,
+                          (size_t)3 * k.ch, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && vis)
+    e = cudaMemcpy2DAsync(vis, (size_t)k.vwidth, k.planes_v, k.vpitch, (size_t)k.vwidth,
+                          (size_t)3 * k.vh, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "frame download");
+  const uint32_t nc = v->host_counts[0], nv = v->host_counts[1];
+  if (delta_c && nc) e = cudaMemcpyAsync(delta_c, k.delta_c, (size_t)nc * 2, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && delta_v && nv)
+    e = cudaMemcpyAsync(delta_v, k.delta_v, (size_t)nv * 2, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "index download");
+  if (counts) {
+    counts[0] = nc;
+    counts[1] = nv;
+  }
+  return PV_OK;
+}
+
+pv_status probe_volume_export_state(pv_volume* v, void* tiles_c, void* tiles_v, uint16_t* last_c,
+                                    uint16_t* last_v, uint64_t* frame, void* stream) {
+  if (!v) return pv_set_error(PV_ERR_INVALID, "export: NULL volume");
+  DeviceGuard g(v->device);
+  cudaStream_t st = as_stream(stream);
+  const pv_dev& k = v->k;
+  cudaError_t e = cudaSuccess;
+  if (tiles_c)
+    e = cudaMemcpyAsync(tiles_c, k.state_c, (size_t)3 * k.P * k.tc * k.tc * v->state_bytes,
+                        cudaMemcpyDefault, st);
+  if (e == cudaSuccess && tiles_v)
+    e = cudaMemcpyAsync(tiles_v, k.state_v, (size_t)2 * k.P * k.tv * k.tv * v->state_bytes,
+                        cudaMemcpyDefault, st);
+  if (e == cudaSuccess && last_c)
+    e = cudaMemcpyAsync(last_c, k.last_c, (size_t)3 * k.P * k.Tc * 2, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && last_v)
+    e = cudaMemcpyAsync(last_v, k.last_v, (size_t)2 * k.P * k.Tv * 2, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "export");
+  if (frame) *frame = v->frame;
+  return PV_OK;
+}
+
+pv_status probe_volume_import_state(pv_volume* v, const void* tiles_c, const void* tiles_v,
+                                    const uint16_t* last_c, const uint16_t* last_v, uint64_t frame,
+                                    void* stream) {
+  if (!v || !tiles_c || !tiles_v || !last_c || !last_v)
+    return pv_set_error(PV_ERR_INVALID, "import: NULL argument");
+  DeviceGuard g(v->device);
+  cudaStream_t st = as_stream(stream);
+  const pv_dev& k = v->k;
+  unsigned long long f = frame;
+  cudaError_t e = cudaMemcpyAsync(k.state_c, tiles_c, (size_t)3 * k.P * k.tc * k.tc * v->state_bytes,
+                                  cudaMemcpyDefault, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(k.state_v, tiles_v, (size_t)2 * k.P * k.tv * k.tv * v->state_bytes,
+                        cudaMemcpyDefault, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(k.last_c, last_c, (size_t)3 * k.P * k.Tc * 2, cudaMemcpyDefault, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(k.last_v, last_v, (size_t)2 * k.P * k.Tv * 2, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(k.frame, &f, sizeof f, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = pv_launch_recompute_flags(k, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "import");
+  v->frame = frame;
+  return PV_OK;
+}
+
+}  // extern "C"

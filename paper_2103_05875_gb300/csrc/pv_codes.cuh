@@ -1,0 +1,122 @@
+// Device-side transmitted codes (Section 3.3 of arXiv 2103.05875) and storage
+// conversions. Integer work only: given identical stored texels the codes are
+// bit-exact with any correct implementation of the same definitions.
+//
+//  * UF10 (default colour code, A2RGB10F's 10-bit unsigned float): 5 exponent
+//    bits (bias 15), 5 mantissa bits. One round-to-nearest-even from the
+//    stored value, subnormals kept, negative / -0 / NaN -> 0, +inf and values
+//    past the largest finite code clamp to 0x3DF.
+//  * UNORM10: round(clamp(x, 0, 1) * 1023), ties to even, evaluated exactly.
+//  * Visibility code: the binary16 bit pattern of the stored value.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/probe_stream.h"
+
+namespace pv {
+
+// Drop `s` low bits of x with round-to-nearest-even (0 < s < 32).
+__device__ __forceinline__ uint32_t rne_shift(uint32_t x, uint32_t s) {
+  uint32_t q = x >> s;
+  uint32_t rem = x & ((1u << s) - 1u);
+  uint32_t half = 1u << (s - 1);
+  return q + ((rem > half) || (rem == half && (q & 1u)));
+}
+
+// UF10 code of a binary16 value given by its bits.
+__device__ __forceinline__ uint32_t uf10_from_half_bits(uint32_t h) {
+  if (h & 0x8000u) return 0u;                         // negative, -0, negative NaN
+  uint32_t e = (h >> 10) & 0x1Fu, m = h & 0x3FFu;
+  if (e == 31u) return m ? 0u : 0x3DFu;               // NaN -> 0, +inf -> top code
+  // binary16 and UF10 share exponent bias and range, so the code is the
+  // magnitude bits with 5 mantissa bits rounded off (subnormals included).
+  uint32_t c = rne_shift(h & 0x7FFFu, 5);
+  return c > 0x3DFu ? 0x3DFu : c;
+}
+
+// UF10 code of a binary32 value given by its bits (one direct rounding).
+__device__ __forceinline__ uint32_t uf10_from_float_bits(uint32_t f) {
+  if (f & 0x80000000u) return 0u;
+  uint32_t e = (f >> 23) & 0xFFu, m = f & 0x7FFFFFu;
+  if (e == 255u) return m ? 0u : 0x3DFu;
+  if (e >= 113u) {                                    // UF10 normal range (exponent >= -14)
+    uint32_t mag = ((e - 112u) << 23) | m;
+    uint32_t c = rne_shift(mag, 18);
+    return c > 0x3DFu ? 0x3DFu : c;
+  }
+  if (e == 0u) return 0u;                             // binary32 subnormal: far below 2^-20
+  // UF10 subnormal: code = round(value / 2^-19), value = (2^23 + m) * 2^(e-150)
+  uint32_t s = 131u - e;                              // >= 19
+  if (s > 31u) return 0u;
+  return rne_shift(0x800000u | m, s);
+}
+
+// round(clamp(x,0,1)*1023) with ties to even, exact for any float x.
+__device__ __forceinline__ uint32_t unorm10_from_float(float x) {
+  if (!(x > 0.0f)) return 0u;                         // also NaN
+  if (x >= 1.0f) return 1023u;
+  float p = x * 1023.0f;
+  float e = fmaf(x, 1023.0f, -p);                     // exact residual of the product
+  float fl = floorf(p);
+  float fr = p - fl;                                  // exact
+  uint32_t k = (uint32_t)fl;
+  if (fr > 0.5f) return k + 1u;
+  if (fr < 0.5f) return k;
+  if (e > 0.0f) return k + 1u;                        // true value above the tie
+  if (e < 0.0f) return k;
+  return k + (k & 1u);                                // exact tie: to even
+}
+
+__device__ __forceinline__ float load_state(const void* base, size_t i, int fmt) {
+  if (fmt == PV_FMT_F16) return __half2float(reinterpret_cast<const __half*>(base)[i]);
+  return reinterpret_cast<const float*>(base)[i];
+}
+
+__device__ __forceinline__ void store_state(void* base, size_t i, float v, int fmt) {
+  if (fmt == PV_FMT_F16) reinterpret_cast<__half*>(base)[i] = __float2half_rn(v);
+  else reinterpret_cast<float*>(base)[i] = v;
+}
+
+// Raw bits of a stored texel (binary16 bits zero-extended, or binary32 bits).
+__device__ __forceinline__ uint32_t load_state_bits(const void* base, size_t i, int fmt) {
+  if (fmt == PV_FMT_F16) return reinterpret_cast<const uint16_t*>(base)[i];
+  return reinterpret_cast<const uint32_t*>(base)[i];
+}
+
+// Colour code of a stored texel.
+__device__ __forceinline__ uint32_t color_code_of(const void* base, size_t i, int fmt, int kind) {
+  uint32_t b = load_state_bits(base, i, fmt);
+  if (kind == PV_CODE_UNORM10) {
+    float x = (fmt == PV_FMT_F16) ? __half2float(__ushort_as_half((unsigned short)b))
+                                  : __uint_as_float(b);
+    return unorm10_from_float(x);
+  }
+  return fmt == PV_FMT_F16 ? uf10_from_half_bits(b) : uf10_from_float_bits(b);
+}
+
+// Visibility code (RG16F channel) of a stored texel.
+__device__ __forceinline__ uint32_t vis_code_of(const void* base, size_t i, int fmt) {
+  uint32_t b = load_state_bits(base, i, fmt);
+  if (fmt == PV_FMT_F16) return b;
+  return __half_as_ushort(__float2half_rn(__uint_as_float(b)));
+}
+
+// Tile positions (row, col in 0..n+1) that copy interior texel (i, j) (0-based),
+// following the octahedral guard-band rule of Section 3.4 (reflection across
+// each edge; corners by double reflection). Returns how many (0..3).
+__device__ __forceinline__ int border_targets(int i, int j, int n, int* tr, int* tc) {
+  int r = i + 1, c = j + 1, k = 0;
+  if (r == 1) { tr[k] = 0; tc[k] = n + 1 - c; ++k; }
+  if (r == n) { tr[k] = n + 1; tc[k] = n + 1 - c; ++k; }
+  if (c == 1) { tr[k] = n + 1 - r; tc[k] = 0; ++k; }
+  if (c == n) { tr[k] = n + 1 - r; tc[k] = n + 1; ++k; }
+  if (r == n && c == n) { tr[k] = 0; tc[k] = 0; ++k; }
+  if (r == n && c == 1) { tr[k] = 0; tc[k] = n + 1; ++k; }
+  if (r == 1 && c == n) { tr[k] = n + 1; tc[k] = 0; ++k; }
+  if (r == 1 && c == 1) { tr[k] = n + 1; tc[k] = n + 1; ++k; }
+  return k;
+}
+
+}  // namespace pv

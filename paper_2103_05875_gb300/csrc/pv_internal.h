@@ -1,0 +1,76 @@
+// Internal definitions shared by the host API and the kernels of the probe
+// streaming library. Not part of the public ABI (see include/probe_stream.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/probe_stream.h"
+
+#define PV_SENTINEL 0xFFFFu   // last-transmitted code of a probe never sent
+
+// Everything a kernel needs to know about a volume, passed by value.
+struct pv_dev {
+  int P, R, nc, nv, tc, tv, Tc, Tv;     // probes, rays, interiors, tiles, texels per tile
+  int bw, bh;                           // update-texture block grid
+  int cpitch, ch;                       // colour plane pitch (bytes) and height
+  int vpitch, vh, vwidth;               // visibility plane pitch (bytes), height, width x'
+  int state_fmt, operand_fmt, color_code, color_shift;
+  float h, sharpness;
+  int first_frame_no_hysteresis;
+  void* state_c;                        // [3][P][tc][tc]
+  void* state_v;                        // [2][P][tv][tv]
+  uint16_t* last_c;                     // [3][P][Tc]
+  uint16_t* last_v;                     // [2][P][Tv]
+  uint8_t* flags;                       // [5][P]: colour R,G,B then d, d^2 changed
+  float* w_rt;                          // [R][Tc + Tv] weights, ray-major (SIMT blend)
+  float* sums;                          // [Tc + Tv] weight sums
+  void* w_op;                           // [(Tc_pad + Tv_pad)][R_pad] weights, texel-major, operand format
+  float* hy;                            // [1] hysteresis of the frame being blended
+  unsigned long long* frame;            // [1] device frame counter
+  uint16_t* idx_c;                      // [P]
+  uint16_t* idx_v;
+  uint16_t* delta_c;
+  uint16_t* delta_v;
+  uint32_t* counts;                     // [4]: count_c, count_v, prev_c, prev_v
+  uint16_t* planes_c;                   // 3 planes of ch rows x cpitch bytes
+  uint8_t* planes_v;                    // 3 planes of vh rows x vpitch bytes
+  int tc_pad, tv_pad, r_pad;            // padded shapes of w_op
+};
+
+struct pv_volume {
+  pv_desc d;
+  pv_dev k;
+  int device;
+  int kernel;
+  int state_bytes, op_bytes;
+  int cwidth;                           // colour plane width in samples
+  char* base;                           // single device allocation
+  size_t bytes;
+  void* stage_rad;                      // staging for probe_update_host
+  void* stage_dist;
+  float* stage_dirs;
+  uint32_t* host_counts;                // pinned [4]
+  unsigned long long frame;             // host mirror of the frame counter
+  void* tc_plan;                        // tensor-core kernel plan (tensor maps), or NULL
+};
+
+// ---------------------------------------------------------------- launchers
+cudaError_t pv_launch_weights(const pv_dev& k, const float* dirs, int want_rt, int want_op,
+                              cudaStream_t s);
+cudaError_t pv_simt_prepare();
+cudaError_t pv_launch_blend_simt(const pv_dev& k, const void* rad, const void* dist,
+                                 cudaStream_t s);
+cudaError_t pv_launch_select(const pv_dev& k, cudaStream_t s);
+cudaError_t pv_launch_pack(const pv_dev& k, cudaStream_t s);
+cudaError_t pv_launch_recompute_flags(const pv_dev& k, cudaStream_t s);
+
+// tensor-core blend (pv_blend_tc.cu)
+bool pv_tc_supported(const pv_desc* d, const char** why);
+cudaError_t pv_tc_plan_create(pv_volume* v);
+void pv_tc_plan_destroy(pv_volume* v);
+cudaError_t pv_launch_blend_tc(pv_volume* v, const void* rad, const void* dist, cudaStream_t s);
+
+// error reporting (pv_api.cpp)
+pv_status pv_set_error(pv_status s, const char* fmt, ...);

@@ -1,0 +1,117 @@
+// K0: per-frame blend weights of a probe volume (Section 3.2 of arXiv
+// 2103.05875, after DDGI): for every colour texel W = max(0, n_t . d_r), for
+// every visibility texel W = max(0, n_t . d_r)^sharpness, plus the weight sums
+// used for normalisation. One block per texel, threads over rays.
+//
+// Accuracy: the octahedral texel direction is q/|q| with an integer vector q
+// (u = a/n, v = b/n with integer a, b), so n_t . d_r is evaluated as a
+// float-float dot product of exact integers with the float32 ray directions,
+// divided by sqrt(|q|^2) in float-float. The cosine is then within half an
+// ulp, and the visibility weight c^s is corrected to first order for the low
+// part of c (s * c_lo / c_hi), which keeps the amplification of the cosine's
+// rounding by the exponent s out of W. Weights are rounded to the operand
+// format (FP16/BF16 precision forms) before they are summed, so each texel's
+// normalisation uses exactly the weights of the contraction.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "pv_internal.h"
+
+namespace {
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float round_operand(float w, int fmt) {
+  if (fmt == PV_FMT_F16) return __half2float(__float2half_rn(w));
+  if (fmt == PV_FMT_BF16) return __bfloat162float(__float2bfloat16_rn(w));
+  return w;
+}
+
+__device__ __forceinline__ void store_operand(void* base, size_t i, float w, int fmt) {
+  if (fmt == PV_FMT_F16) reinterpret_cast<__half*>(base)[i] = __float2half_rn(w);
+  else if (fmt == PV_FMT_BF16) reinterpret_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn(w);
+  else reinterpret_cast<float*>(base)[i] = w;
+}
+
+__global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restrict__ dirs,
+                                                 int want_rt, int want_op) {
+  const int T = k.Tc + k.Tv;
+  const int tg = blockIdx.x;
+  const bool vis = tg >= k.Tc;
+  const int n = vis ? k.nv : k.nc;
+  const int t = vis ? tg - k.Tc : tg;
+  const int i = t / n, j = t % n;
+  const int a = 2 * j + 1 - n, b = 2 * i + 1 - n;
+  const int z = n - abs(a) - abs(b);
+  const int x = z < 0 ? (n - abs(b)) * (a >= 0 ? 1 : -1) : a;
+  const int y = z < 0 ? (n - abs(a)) * (b >= 0 ? 1 : -1) : b;
+  const float fx = (float)x, fy = (float)y, fz = (float)z;
+  const float Q = (float)(x * x + y * y + z * z);       // exact small integer
+  const float sq = sqrtf(Q);
+  const float sq_lo = fmaf(-sq, sq, Q) / (2.0f * sq);   // sqrt(Q) ~= sq + sq_lo
+  const float s = k.sharpness;
+
+  // Operand-format copy for the tensor-core blend: texel-major rows of r_pad
+  // rays; colour rows first (tc_pad of them), then visibility rows.
+  const size_t op_row = vis ? (size_t)(k.tc_pad + t) : (size_t)t;
+
+  float part = 0.0f;
+  for (int r = threadIdx.x; r < k.R; r += blockDim.x) {
+    const float dx = dirs[3 * r + 0], dy = dirs[3 * r + 1], dz = dirs[3 * r + 2];
+    float p1, e1, p2, e2, p3, e3, s12, f12, sd, f3;
+    two_prod(fx, dx, p1, e1);
+    two_prod(fy, dy, p2, e2);
+    two_prod(fz, dz, p3, e3);
+    two_sum(p1, p2, s12, f12);
+    two_sum(s12, p3, sd, f3);
+    const float sd_lo = ((e1 + e2) + e3) + (f12 + f3);   // q . d ~= sd + sd_lo
+    const float c0 = sd / sq;
+    float rem = fmaf(-c0, sq, sd);                        // exact remainder of the division
+    rem = (rem + sd_lo) - c0 * sq_lo;
+    const float c1 = rem / sq;
+    float c_hi, c_lo;
+    two_sum(c0, c1, c_hi, c_lo);                          // cosine as a float-float
+    float w;
+    if (!vis) {
+      w = c_hi > 0.0f ? c_hi : 0.0f;
+    } else {
+      w = c_hi > 0.0f ? powf(c_hi, s) * fmaf(s, c_lo / c_hi, 1.0f) : 0.0f;
+    }
+    w = round_operand(w, k.operand_fmt);
+    if (want_rt) k.w_rt[(size_t)r * T + tg] = w;
+    if (want_op) store_operand(k.w_op, op_row * k.r_pad + r, w, k.operand_fmt);
+    part += w;
+  }
+  // deterministic block reduction of the weight sum
+  __shared__ float red[256];
+  red[threadIdx.x] = part;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) k.sums[tg] = red[0];
+
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long f = *k.frame;
+    *k.hy = (f == 0ull && k.first_frame_no_hysteresis) ? 0.0f : k.h;
+    *k.frame = f + 1ull;
+  }
+}
+
+}  // namespace
+
+cudaError_t pv_launch_weights(const pv_dev& k, const float* dirs, int want_rt, int want_op,
+                              cudaStream_t st) {
+  k_weights<<<k.Tc + k.Tv, 256, 0, st>>>(k, dirs, want_rt, want_op);
+  return cudaGetLastError();
+}

@@ -1,0 +1,65 @@
+"""CPU-side checks of the C ABI library: it builds for sm_103a, loads, and exports every
+function include/*.h declares; host-only entry points behave (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_2103_05875_gb300 import build as b
+    path = b.build()
+    return ctypes.CDLL(path), path
+
+
+def _declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\**\s+\**([A-Za-z_]\w*)\s*\(", text, re.M):
+            if m.group(1) not in ("if", "while", "for", "return", "sizeof"):
+                names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_path_entry_points():
+    names = _declared_functions()
+    for required in ("probe_volume_create", "probe_update", "probe_select_and_pack",
+                     "probe_volume_destroy", "pv_ray_directions"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    lib, path = built_lib
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"{path} lacks {missing}"
+
+
+def test_library_targets_sm_103a(built_lib):
+    from paper_2103_05875_gb300 import build as b
+    assert "arch=compute_103a,code=sm_103a" in " ".join(b.ARCH)
+
+
+def test_host_only_entry_points(built_lib):
+    import paper_2103_05875_gb300 as pv
+    import pv_workload as wl
+    d = pv.pv_ray_directions(42, 3, 7, 256)
+    ref = wl.ray_directions(42, 3, 7, 256)
+    assert np.abs(d - ref).max() < 1e-6
+    np.testing.assert_allclose(np.linalg.norm(d.astype(np.float64), axis=1), 1.0, atol=1e-6)
+    n = pv.probe_volume_bytes(pv.make_desc(wl.config2()))
+    assert 10e6 < n < 40e6
+    with pytest.raises(pv.PVError) as e:
+        pv.probe_volume_bytes(pv.make_desc(wl.config2(), nx=64, ny=64, nz=64))
+    assert e.value.status == -6
+    with pytest.raises(pv.PVError) as e:
+        pv.probe_volume_bytes(pv.make_desc(wl.config2(), hysteresis=1.5))
+    assert e.value.status == -1
+    assert pv.lib.pv_status_string(-5) == b"PV_ERR_TIMEOUT"
