@@ -41,9 +41,10 @@ struct Layout {
   int cwidth, cheight, cpitch, vwidth, vheight, vpitch;
   int tc_pad, tv_pad, r_pad;
   int sb, ob;
+  int sc_stride, sv_stride, lc_stride, lv_stride;
   size_t off_state_c, off_state_v, off_last_c, off_last_v, off_flags, off_wrt, off_sums, off_wop,
       off_hy, off_frame, off_idx_c, off_idx_v, off_delta_c, off_delta_v, off_counts, off_planes_c,
-      off_planes_v, total;
+      off_planes_v, off_err, total;
 };
 
 pv_status validate(const pv_desc* d) {
@@ -100,16 +101,22 @@ Layout layout_of(const pv_desc* d) {
   L.r_pad = (int)round_up((size_t)L.R, 64);
   L.sb = d->state_fmt == PV_FMT_F16 ? 2 : 4;
   L.ob = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
+  // per-probe strides padded to 16 bytes so each probe's tile and code row can
+  // be moved by bulk copies
+  L.sc_stride = (int)round_up((size_t)L.tc * L.tc, 16 / L.sb);
+  L.sv_stride = (int)round_up((size_t)L.tv * L.tv, 16 / L.sb);
+  L.lc_stride = (int)round_up((size_t)L.Tc, 8);
+  L.lv_stride = (int)round_up((size_t)L.Tv, 8);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t at = off;
     off = round_up(off + bytes, 256);
     return at;
   };
-  L.off_state_c = take((size_t)3 * L.P * L.tc * L.tc * L.sb);
-  L.off_state_v = take((size_t)2 * L.P * L.tv * L.tv * L.sb);
-  L.off_last_c = take((size_t)3 * L.P * L.Tc * 2);
-  L.off_last_v = take((size_t)2 * L.P * L.Tv * 2);
+  L.off_state_c = take((size_t)3 * L.P * L.sc_stride * L.sb);
+  L.off_state_v = take((size_t)2 * L.P * L.sv_stride * L.sb);
+  L.off_last_c = take((size_t)3 * L.P * L.lc_stride * 2);
+  L.off_last_v = take((size_t)2 * L.P * L.lv_stride * 2);
   L.off_flags = take((size_t)5 * L.P);
   L.off_wrt = take((size_t)L.R * (L.Tc + L.Tv) * 4);
   L.off_sums = take((size_t)(L.Tc + L.Tv) * 4);
@@ -123,6 +130,7 @@ Layout layout_of(const pv_desc* d) {
   L.off_counts = take(16);
   L.off_planes_c = take((size_t)3 * L.cheight * L.cpitch);
   L.off_planes_v = take((size_t)3 * L.vheight * L.vpitch);
+  L.off_err = take(16);
   L.total = off;
   return L;
 }
@@ -232,11 +240,14 @@ pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
   k.planes_c = (uint16_t*)(b + L.off_planes_c);
   k.planes_v = (uint8_t*)(b + L.off_planes_v);
   k.tc_pad = L.tc_pad; k.tv_pad = L.tv_pad; k.r_pad = L.r_pad;
+  k.sc_stride = L.sc_stride; k.sv_stride = L.sv_stride;
+  k.lc_stride = L.lc_stride; k.lv_stride = L.lv_stride;
+  k.err = (int*)(b + L.off_err);
 
   // zero everything, then mark every probe "never sent"
   e = cudaMemset(v->base, 0, L.total);
-  if (e == cudaSuccess) e = cudaMemset(k.last_c, 0xFF, (size_t)3 * L.P * L.Tc * 2);
-  if (e == cudaSuccess) e = cudaMemset(k.last_v, 0xFF, (size_t)2 * L.P * L.Tv * 2);
+  if (e == cudaSuccess) e = cudaMemset(k.last_c, 0xFF, (size_t)3 * L.P * L.lc_stride * 2);
+  if (e == cudaSuccess) e = cudaMemset(k.last_v, 0xFF, (size_t)2 * L.P * L.lv_stride * 2);
   if (e == cudaSuccess) e = pv_simt_prepare();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess && kernel == PV_KERNEL_TCGEN05) e = pv_tc_plan_create(v);
@@ -403,17 +414,21 @@ pv_status probe_volume_export_state(pv_volume* v, void* tiles_c, void* tiles_v, 
   DeviceGuard g(v->device);
   cudaStream_t st = as_stream(stream);
   const pv_dev& k = v->k;
+  const size_t sb = v->state_bytes;
+  const size_t tcc = (size_t)k.tc * k.tc, tvv = (size_t)k.tv * k.tv;
   cudaError_t e = cudaSuccess;
   if (tiles_c)
-    e = cudaMemcpyAsync(tiles_c, k.state_c, (size_t)3 * k.P * k.tc * k.tc * v->state_bytes,
-                        cudaMemcpyDefault, st);
+    e = cudaMemcpy2DAsync(tiles_c, tcc * sb, k.state_c, (size_t)k.sc_stride * sb, tcc * sb,
+                          (size_t)3 * k.P, cudaMemcpyDefault, st);
   if (e == cudaSuccess && tiles_v)
-    e = cudaMemcpyAsync(tiles_v, k.state_v, (size_t)2 * k.P * k.tv * k.tv * v->state_bytes,
-                        cudaMemcpyDefault, st);
+    e = cudaMemcpy2DAsync(tiles_v, tvv * sb, k.state_v, (size_t)k.sv_stride * sb, tvv * sb,
+                          (size_t)2 * k.P, cudaMemcpyDefault, st);
   if (e == cudaSuccess && last_c)
-    e = cudaMemcpyAsync(last_c, k.last_c, (size_t)3 * k.P * k.Tc * 2, cudaMemcpyDefault, st);
+    e = cudaMemcpy2DAsync(last_c, (size_t)k.Tc * 2, k.last_c, (size_t)k.lc_stride * 2,
+                          (size_t)k.Tc * 2, (size_t)3 * k.P, cudaMemcpyDefault, st);
   if (e == cudaSuccess && last_v)
-    e = cudaMemcpyAsync(last_v, k.last_v, (size_t)2 * k.P * k.Tv * 2, cudaMemcpyDefault, st);
+    e = cudaMemcpy2DAsync(last_v, (size_t)k.Tv * 2, k.last_v, (size_t)k.lv_stride * 2,
+                          (size_t)k.Tv * 2, (size_t)2 * k.P, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "export");
   if (frame) *frame = v->frame;
@@ -429,15 +444,19 @@ pv_status probe_volume_import_state(pv_volume* v, const void* tiles_c, const voi
   cudaStream_t st = as_stream(stream);
   const pv_dev& k = v->k;
   unsigned long long f = frame;
-  cudaError_t e = cudaMemcpyAsync(k.state_c, tiles_c, (size_t)3 * k.P * k.tc * k.tc * v->state_bytes,
-                                  cudaMemcpyDefault, st);
+  const size_t sb = v->state_bytes;
+  const size_t tcc = (size_t)k.tc * k.tc, tvv = (size_t)k.tv * k.tv;
+  cudaError_t e = cudaMemcpy2DAsync(k.state_c, (size_t)k.sc_stride * sb, tiles_c, tcc * sb, tcc * sb,
+                                    (size_t)3 * k.P, cudaMemcpyDefault, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(k.state_v, tiles_v, (size_t)2 * k.P * k.tv * k.tv * v->state_bytes,
-                        cudaMemcpyDefault, st);
+    e = cudaMemcpy2DAsync(k.state_v, (size_t)k.sv_stride * sb, tiles_v, tvv * sb, tvv * sb,
+                          (size_t)2 * k.P, cudaMemcpyDefault, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(k.last_c, last_c, (size_t)3 * k.P * k.Tc * 2, cudaMemcpyDefault, st);
+    e = cudaMemcpy2DAsync(k.last_c, (size_t)k.lc_stride * 2, last_c, (size_t)k.Tc * 2,
+                          (size_t)k.Tc * 2, (size_t)3 * k.P, cudaMemcpyDefault, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(k.last_v, last_v, (size_t)2 * k.P * k.Tv * 2, cudaMemcpyDefault, st);
+    e = cudaMemcpy2DAsync(k.last_v, (size_t)k.lv_stride * 2, last_v, (size_t)k.Tv * 2,
+                          (size_t)k.Tv * 2, (size_t)2 * k.P, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(k.frame, &f, sizeof f, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = pv_launch_recompute_flags(k, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

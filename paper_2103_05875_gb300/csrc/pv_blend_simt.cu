@@ -34,17 +34,26 @@ __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v)
 template <>
 __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+// d^2 as the contraction sees it: formed on chip from the operand-format d and
+// represented as hi + lo in the operand format (binary16 with a 2^-8 scale,
+// undone here, so that d up to 4096 stays in range; bfloat16 unscaled).
 template <typename Tin>
 __device__ __forceinline__ float square_operand(float d);
 template <>
 __device__ __forceinline__ float square_operand<float>(float d) { return d * d; }
 template <>
 __device__ __forceinline__ float square_operand<__half>(float d) {
-  return __half2float(__float2half_rn(d * d));
+  const float q = d * d * 0.00390625f;                 // exact: d has 11 significant bits
+  const float hi = __half2float(__float2half_rn(q));
+  const float lo = __half2float(__float2half_rn(q - hi));
+  return (hi + lo) * 256.0f;
 }
 template <>
 __device__ __forceinline__ float square_operand<__nv_bfloat16>(float d) {
-  return __bfloat162float(__float2bfloat16_rn(d * d));
+  const float q = d * d;                                // exact: d has 8 significant bits
+  const float hi = __bfloat162float(__float2bfloat16_rn(q));
+  const float lo = __bfloat162float(__float2bfloat16_rn(q - hi));
+  return hi + lo;
 }
 
 template <typename Tin>
@@ -114,7 +123,8 @@ __global__ void __launch_bounds__(NT) k_blend_simt(pv_dev k, const Tin* __restri
     }
   }
 
-  // fused epilogue
+  // fused epilogue: loads of old texels and last codes are issued for all G
+  // probes of a unit before any of them is used
   const float h = *k.hy;
   const float one_m_h = 1.0f - h;
 #pragma unroll
@@ -130,30 +140,36 @@ __global__ void __launch_bounds__(NT) k_blend_simt(pv_dev k, const Tin* __restri
     const float S = k.sums[(vis ? k.Tc : 0) + t];
     void* st = vis ? k.state_v : k.state_c;
     const uint16_t* last = vis ? k.last_v : k.last_c;
-    const int T_here = vis ? k.Tv : k.Tc;
+    const int sstride = vis ? k.sv_stride : k.sc_stride;
+    const int lstride = vis ? k.lv_stride : k.lc_stride;
+    const int pos = (i + 1) * tile + (j + 1);
     int tr[8], tcl[8];
     const int nb = pv::border_targets(i, j, n, tr, tcl);
+    uint32_t oldb[G];
+    uint32_t prev[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int p = min(p0 + g, k.P - 1);
+      oldb[g] = pv::load_state_bits(st, ((size_t)ch * k.P + p) * sstride + pos, k.state_fmt);
+      prev[g] = last[((size_t)ch * k.P + p) * lstride + t];
+    }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int p = p0 + g;
-      if (p >= k.P) break;
-      const size_t tile0 = ((size_t)ch * k.P + p) * tile * tile;
-      const size_t at = tile0 + (size_t)(i + 1) * tile + (j + 1);
-      float nv;
+      if (p >= k.P) continue;
+      const size_t tile0 = ((size_t)ch * k.P + p) * sstride;
+      uint32_t nb_bits = oldb[g];
       if (S > 0.0f) {
         const float m = acc[q][g] / S;
-        const float old = pv::load_state(st, at, k.state_fmt);
-        nv = fmaf(h, old, one_m_h * m);
-        pv::store_state(st, at, nv, k.state_fmt);
+        const float old = pv::state_value_of_bits(oldb[g], k.state_fmt);
+        nb_bits = pv::state_bits_of(fmaf(h, old, one_m_h * m), k.state_fmt);
+        pv::store_state_bits(st, tile0 + pos, nb_bits, k.state_fmt);
       }
-      // (a texel with zero weight sum keeps its stored value; re-copy it anyway)
-      const float stored = pv::load_state(st, at, k.state_fmt);
       for (int b = 0; b < nb; ++b)
-        pv::store_state(st, tile0 + (size_t)tr[b] * tile + tcl[b], stored, k.state_fmt);
-      const uint32_t code = vis ? pv::vis_code_of(st, at, k.state_fmt)
-                                : pv::color_code_of(st, at, k.state_fmt, k.color_code);
-      const uint32_t prev = last[((size_t)ch * k.P + p) * T_here + t];
-      if (code != prev) flag_s[((vis ? 3 : 0) + ch) * G + g] = 1;
+        pv::store_state_bits(st, tile0 + (size_t)tr[b] * tile + tcl[b], nb_bits, k.state_fmt);
+      const uint32_t code = vis ? pv::vis_code_of_bits(nb_bits, k.state_fmt)
+                                : pv::color_code_of_bits(nb_bits, k.state_fmt, k.color_code);
+      if (code != prev[g]) flag_s[((vis ? 3 : 0) + ch) * G + g] = 1;
     }
   }
   __syncthreads();

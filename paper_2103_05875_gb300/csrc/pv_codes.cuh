@@ -85,27 +85,47 @@ __device__ __forceinline__ uint32_t load_state_bits(const void* base, size_t i, 
   return reinterpret_cast<const uint32_t*>(base)[i];
 }
 
+__device__ __forceinline__ uint32_t color_code_of_bits(uint32_t b, int fmt, int kind);
+__device__ __forceinline__ uint32_t vis_code_of_bits(uint32_t b, int fmt);
+
 // Colour code of a stored texel.
 __device__ __forceinline__ uint32_t color_code_of(const void* base, size_t i, int fmt, int kind) {
-  uint32_t b = load_state_bits(base, i, fmt);
-  if (kind == PV_CODE_UNORM10) {
-    float x = (fmt == PV_FMT_F16) ? __half2float(__ushort_as_half((unsigned short)b))
-                                  : __uint_as_float(b);
-    return unorm10_from_float(x);
-  }
-  return fmt == PV_FMT_F16 ? uf10_from_half_bits(b) : uf10_from_float_bits(b);
+  return color_code_of_bits(load_state_bits(base, i, fmt), fmt, kind);
 }
 
 // Visibility code (RG16F channel) of a stored texel.
 __device__ __forceinline__ uint32_t vis_code_of(const void* base, size_t i, int fmt) {
-  uint32_t b = load_state_bits(base, i, fmt);
+  return vis_code_of_bits(load_state_bits(base, i, fmt), fmt);
+}
+
+// Bits of a blended value once rounded to the state format.
+__device__ __forceinline__ uint32_t state_bits_of(float v, int fmt) {
+  return fmt == PV_FMT_F16 ? (uint32_t)__half_as_ushort(__float2half_rn(v)) : __float_as_uint(v);
+}
+
+__device__ __forceinline__ void store_state_bits(void* base, size_t i, uint32_t b, int fmt) {
+  if (fmt == PV_FMT_F16) reinterpret_cast<uint16_t*>(base)[i] = (uint16_t)b;
+  else reinterpret_cast<uint32_t*>(base)[i] = b;
+}
+
+__device__ __forceinline__ float state_value_of_bits(uint32_t b, int fmt) {
+  return fmt == PV_FMT_F16 ? __half2float(__ushort_as_half((unsigned short)b)) : __uint_as_float(b);
+}
+
+__device__ __forceinline__ uint32_t color_code_of_bits(uint32_t b, int fmt, int kind) {
+  if (kind == PV_CODE_UNORM10) return unorm10_from_float(state_value_of_bits(b, fmt));
+  return fmt == PV_FMT_F16 ? uf10_from_half_bits(b) : uf10_from_float_bits(b);
+}
+
+__device__ __forceinline__ uint32_t vis_code_of_bits(uint32_t b, int fmt) {
   if (fmt == PV_FMT_F16) return b;
   return __half_as_ushort(__float2half_rn(__uint_as_float(b)));
 }
 
 // Tile positions (row, col in 0..n+1) that copy interior texel (i, j) (0-based),
 // following the octahedral guard-band rule of Section 3.4 (reflection across
-// each edge; corners by double reflection). Returns how many (0..3).
+// each edge; corners by double reflection). Returns how many (at most 3 for
+// n >= 2; all eight guard texels for n = 1).
 __device__ __forceinline__ int border_targets(int i, int j, int n, int* tr, int* tc) {
   int r = i + 1, c = j + 1, k = 0;
   if (r == 1) { tr[k] = 0; tc[k] = n + 1 - c; ++k; }

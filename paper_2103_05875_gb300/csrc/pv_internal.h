@@ -19,14 +19,15 @@ struct pv_dev {
   int state_fmt, operand_fmt, color_code, color_shift;
   float h, sharpness;
   int first_frame_no_hysteresis;
-  void* state_c;                        // [3][P][tc][tc]
-  void* state_v;                        // [2][P][tv][tv]
-  uint16_t* last_c;                     // [3][P][Tc]
-  uint16_t* last_v;                     // [2][P][Tv]
+  void* state_c;                        // [3][P][sc_stride], tile tc x tc at the start of each stride
+  void* state_v;                        // [2][P][sv_stride]
+  uint16_t* last_c;                     // [3][P][lc_stride], first Tc codes used
+  uint16_t* last_v;                     // [2][P][lv_stride]
   uint8_t* flags;                       // [5][P]: colour R,G,B then d, d^2 changed
   float* w_rt;                          // [R][Tc + Tv] weights, ray-major (SIMT blend)
   float* sums;                          // [Tc + Tv] weight sums
-  void* w_op;                           // [(Tc_pad + Tv_pad)][R_pad] weights, texel-major, operand format
+  void* w_op;                           // [planes][tc_pad + tv_pad][r_pad] weights, texel-major, operand
+                                        // format: F16 one plane; BF16 and F32 hi and lo planes
   float* hy;                            // [1] hysteresis of the frame being blended
   unsigned long long* frame;            // [1] device frame counter
   uint16_t* idx_c;                      // [P]
@@ -37,6 +38,9 @@ struct pv_dev {
   uint16_t* planes_c;                   // 3 planes of ch rows x cpitch bytes
   uint8_t* planes_v;                    // 3 planes of vh rows x vpitch bytes
   int tc_pad, tv_pad, r_pad;            // padded shapes of w_op
+  int sc_stride, sv_stride;             // elements per probe tile in state memory (16-byte multiple)
+  int lc_stride, lv_stride;             // codes per probe in the last-transmitted arrays (multiple of 8)
+  int* err;                             // [1] device error word (non-zero: a bounded wait gave up)
 };
 
 struct pv_volume {

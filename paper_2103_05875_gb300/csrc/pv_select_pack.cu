@@ -28,7 +28,7 @@ constexpr int SCAN_THREADS = 1024;
 __global__ void __launch_bounds__(SCAN_THREADS) k_select(pv_dev k) {
   const int which = blockIdx.x;                  // 0 colour, 1 visibility
   const int nch = which ? 2 : 3;
-  const uint8_t* flags = k.flags + (size_t)(which ? 3 : 0) * k.P;
+  uint8_t* flags = k.flags + (size_t)(which ? 3 : 0) * k.P;
   uint16_t* idx = which ? k.idx_v : k.idx_c;
   uint16_t* delta = which ? k.delta_v : k.delta_c;
   const int tid = threadIdx.x;
@@ -71,6 +71,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_select(pv_dev k) {
     for (int c = 0; c < nch; ++c) f |= flags[(size_t)c * k.P + p];
     if (f) idx[slot++] = (uint16_t)p;
   }
+  // every changed probe is sent now, so no flag stays raised: a second
+  // select without a new update selects nothing
+  for (int p = b; p < e; ++p)
+    for (int c = 0; c < nch; ++c) flags[(size_t)c * k.P + p] = 0;
   __syncthreads();                               // idx visible block-wide
   for (int s = excl; s < excl + local; ++s)
     delta[s] = (uint16_t)(s ? (int)idx[s] - (int)idx[s - 1] : (int)idx[s]);
@@ -95,8 +99,8 @@ __global__ void __launch_bounds__(256) k_pack_color(pv_dev k) {
       (size_t)bx * k.nc;
   if (slot < cnt) {
     const int p = k.idx_c[slot];
-    const size_t row0 = (((size_t)c * k.P + p) * k.tc + (i + 1)) * k.tc + 1;
-    uint16_t* last = k.last_c + ((size_t)c * k.P + p) * k.Tc + (size_t)i * k.nc;
+    const size_t row0 = ((size_t)c * k.P + p) * k.sc_stride + (size_t)(i + 1) * k.tc + 1;
+    uint16_t* last = k.last_c + ((size_t)c * k.P + p) * k.lc_stride + (size_t)i * k.nc;
     for (int j = 0; j < k.nc; ++j) {
       const uint32_t code = pv::color_code_of(k.state_c, row0 + j, k.state_fmt, k.color_code);
       dst[j] = (uint16_t)(code << k.color_shift);
@@ -128,12 +132,13 @@ __global__ void __launch_bounds__(256) k_pack_vis(pv_dev k) {
       if (slot < lim) touched = true;
       if (slot < cnt) {
         const int p = k.idx_v[slot];
-        const size_t at0 = (((size_t)p) * k.tv + (i + 1)) * k.tv + (j + 1);
-        const size_t at1 = (((size_t)k.P + p) * k.tv + (i + 1)) * k.tv + (j + 1);
+        const size_t off = (size_t)(i + 1) * k.tv + (j + 1);
+        const size_t at0 = (size_t)p * k.sv_stride + off;
+        const size_t at1 = ((size_t)k.P + p) * k.sv_stride + off;
         const uint32_t c0 = pv::vis_code_of(k.state_v, at0, k.state_fmt);
         const uint32_t c1 = pv::vis_code_of(k.state_v, at1, k.state_fmt);
-        k.last_v[(size_t)p * k.Tv + (size_t)i * k.nv + j] = (uint16_t)c0;
-        k.last_v[((size_t)k.P + p) * k.Tv + (size_t)i * k.nv + j] = (uint16_t)c1;
+        k.last_v[(size_t)p * k.lv_stride + (size_t)i * k.nv + j] = (uint16_t)c0;
+        k.last_v[((size_t)k.P + p) * k.lv_stride + (size_t)i * k.nv + j] = (uint16_t)c1;
         lo0 = c0 & 0xFFu; hi0 = c0 >> 8; lo1 = c1 & 0xFFu; hi1 = c1 >> 8;
       }
     }
@@ -160,10 +165,11 @@ __global__ void __launch_bounds__(256) k_recompute_flags(pv_dev k) {
   const int ch = vis ? ch5 - 3 : ch5;
   const int n = vis ? k.nv : k.nc, tile = n + 2, T = n * n;
   const void* st = vis ? k.state_v : k.state_c;
-  const uint16_t* last = (vis ? k.last_v : k.last_c) + ((size_t)ch * k.P + p) * T;
+  const int sstride = vis ? k.sv_stride : k.sc_stride;
+  const uint16_t* last = (vis ? k.last_v : k.last_c) + ((size_t)ch * k.P + p) * (vis ? k.lv_stride : k.lc_stride);
   int f = 0;
   for (int t = 0; t < T; ++t) {
-    const size_t at = (((size_t)ch * k.P + p) * tile + (t / n + 1)) * tile + (t % n + 1);
+    const size_t at = ((size_t)ch * k.P + p) * sstride + (size_t)(t / n + 1) * tile + (t % n + 1);
     const uint32_t code = vis ? pv::vis_code_of(st, at, k.state_fmt)
                               : pv::color_code_of(st, at, k.state_fmt, k.color_code);
     f |= code != last[t];

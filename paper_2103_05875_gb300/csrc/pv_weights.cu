@@ -3,6 +3,14 @@
 // every visibility texel W = max(0, n_t . d_r)^sharpness, plus the weight sums
 // used for normalisation. One block per texel, threads over rays.
 //
+// Operand forms. FP32: the SIMT blend uses W as is; the tensor-core blend gets
+// W = hi + lo with hi = W truncated to TF32 and lo = W - hi (three TF32
+// products recover FP32 accuracy). FP16: W in binary16, visibility weights
+// scaled by 2^15 so that cos^s does not underflow (the scale cancels in the
+// normalisation). BF16: W = hi + lo, both bfloat16 (two products), since one
+// bfloat16 weight alone is only good to 2^-9. The weight sums always add the
+// effective (rounded) weights, so every texel's mean stays a convex combination.
+//
 // Accuracy: the octahedral texel direction is q/|q| with an integer vector q
 // (u = a/n, v = b/n with integer a, b), so n_t . d_r is evaluated as a
 // float-float dot product of exact integers with the float32 ray directions,
@@ -30,13 +38,34 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-__device__ __forceinline__ float round_operand(float w, int fmt) {
-  if (fmt == PV_FMT_F16) return __half2float(__float2half_rn(w));
-  if (fmt == PV_FMT_BF16) return __bfloat162float(__float2bfloat16_rn(w));
-  return w;
+constexpr float kVisScaleF16 = 32768.0f;   // 2^15
+
+// Effective weight of the operand form, and its operand planes.
+struct OpWeight {
+  float eff;       // value the contraction effectively multiplies with
+  float hi, lo;    // plane values (lo unused for F16)
+};
+
+__device__ __forceinline__ OpWeight split_weight(float w, int fmt, bool vis) {
+  OpWeight o;
+  if (fmt == PV_FMT_F16) {
+    const float s = vis ? kVisScaleF16 : 1.0f;
+    o.hi = __half2float(__float2half_rn(w * s));
+    o.lo = 0.0f;
+    o.eff = o.hi;
+  } else if (fmt == PV_FMT_BF16) {
+    o.hi = __bfloat162float(__float2bfloat16_rn(w));
+    o.lo = __bfloat162float(__float2bfloat16_rn(w - o.hi));
+    o.eff = o.hi + o.lo;                           // exact in binary32
+  } else {
+    o.hi = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);   // TF32 truncation
+    o.lo = w - o.hi;                               // exact
+    o.eff = w;
+  }
+  return o;
 }
 
-__device__ __forceinline__ void store_operand(void* base, size_t i, float w, int fmt) {
+__device__ __forceinline__ void store_plane(void* base, size_t i, float w, int fmt) {
   if (fmt == PV_FMT_F16) reinterpret_cast<__half*>(base)[i] = __float2half_rn(w);
   else if (fmt == PV_FMT_BF16) reinterpret_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn(w);
   else reinterpret_cast<float*>(base)[i] = w;
@@ -63,6 +92,7 @@ __global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restri
   // Operand-format copy for the tensor-core blend: texel-major rows of r_pad
   // rays; colour rows first (tc_pad of them), then visibility rows.
   const size_t op_row = vis ? (size_t)(k.tc_pad + t) : (size_t)t;
+  const size_t plane = (size_t)(k.tc_pad + k.tv_pad) * k.r_pad;   // elements per operand plane
 
   float part = 0.0f;
   for (int r = threadIdx.x; r < k.R; r += blockDim.x) {
@@ -86,10 +116,14 @@ __global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restri
     } else {
       w = c_hi > 0.0f ? powf(c_hi, s) * fmaf(s, c_lo / c_hi, 1.0f) : 0.0f;
     }
-    w = round_operand(w, k.operand_fmt);
-    if (want_rt) k.w_rt[(size_t)r * T + tg] = w;
-    if (want_op) store_operand(k.w_op, op_row * k.r_pad + r, w, k.operand_fmt);
-    part += w;
+    const OpWeight o = split_weight(w, k.operand_fmt, vis);
+    if (want_rt) k.w_rt[(size_t)r * T + tg] = o.eff;
+    if (want_op) {
+      store_plane(k.w_op, op_row * k.r_pad + r, o.hi, k.operand_fmt);
+      if (k.operand_fmt != PV_FMT_F16)
+        store_plane(k.w_op, plane + op_row * k.r_pad + r, o.lo, k.operand_fmt);
+    }
+    part += o.eff;
   }
   // deterministic block reduction of the weight sum
   __shared__ float red[256];

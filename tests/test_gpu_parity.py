@@ -107,8 +107,10 @@ def test_blend_mean_accuracy_full_size(operand_fmt, tol, kernel):
 
 
 def test_config2_sixty_frames_with_step_change():
-    """16^3 probes, 256 rays, FP16 state, 60 frames, 20% of probes x4 at frame 30."""
-    spec = wl.config2()
+    """16^3 probes, 256 rays, FP16 state, 60 frames, 20% of probes x4 at frame 30; rays held
+    fixed and the first frame taken without hysteresis (converged server, Section 3.4)."""
+    import dataclasses
+    spec = dataclasses.replace(wl.config2(), first_frame_no_hysteresis=True)
     vol = H.lib().ProbeVolume(spec)
     fs = wl.FrameStream(spec, wl.config_seed(2), mode="stationary")
     free = OracleVolume(spec)
@@ -125,6 +127,7 @@ def test_config2_sixty_frames_with_step_change():
             assert H.fp16_ulp_diff(tv, free.tiles_v).max() <= 1
     c = np.array(counts)
     assert c[0, 0] == c[0, 1] == 4096
+    assert c[1:30, 0].max() == 0 and c[1:, 1].max() == 0      # converged: nothing to resend
     stepped = wl.step_mask(wl.config_seed(2), 0, 4096, 0.2).sum()
     assert c[30, 0] >= stepped and c[30, 1] == 0
     # GPU and oracle select the same number of probes to within a handful (texels may
