@@ -190,7 +190,9 @@ pv_status probe_update_blend(pv_volume* vol, const void* radiance, const void* d
  * index buffers, writes the colour and visibility planes, and writes the sent
  * codes to the last-transmitted textures. Asynchronous unless
  * want_host_counts != 0, in which case the call waits for the stream and
- * fills out->count_c / count_v. out: host pv_frame.
+ * fills out->count_c / count_v, and returns PV_ERR_TIMEOUT if a bounded
+ * wait inside the tensor-core blend kernel expired (its results are then
+ * invalid; the volume stays usable). out: host pv_frame.
  */
 pv_status probe_select_and_pack(pv_volume* vol, pv_frame* out, int32_t want_host_counts,
                                 void* stream);

@@ -120,7 +120,9 @@ Layout layout_of(const pv_desc* d) {
   L.off_flags = take((size_t)5 * L.P);
   L.off_wrt = take((size_t)L.R * (L.Tc + L.Tv) * 4);
   L.off_sums = take((size_t)(L.Tc + L.Tv) * 4);
-  L.off_wop = take((size_t)(L.tc_pad + L.tv_pad) * L.r_pad * (d->operand_fmt == PV_FMT_F32 ? 8 : 2));
+  // operand weights: F16 one binary16 plane, BF16 hi + lo bfloat16 planes, F32 hi + lo float planes
+  const size_t wop_elem = d->operand_fmt == PV_FMT_F32 ? 8 : (d->operand_fmt == PV_FMT_BF16 ? 4 : 2);
+  L.off_wop = take((size_t)(L.tc_pad + L.tv_pad) * L.r_pad * wop_elem);
   L.off_hy = take(16);
   L.off_frame = take(16);
   L.off_idx_c = take((size_t)L.P * 2);
@@ -345,10 +347,15 @@ pv_status probe_select_and_pack(pv_volume* v, pv_frame* out, int32_t want_host_c
   out->frame = v->frame;
   if (want_host_counts) {
     e = cudaMemcpyAsync(v->host_counts, v->k.counts, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(v->host_counts + 2, v->k.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "count readback");
     out->count_c = v->host_counts[0];
     out->count_v = v->host_counts[1];
+    if (v->host_counts[2])
+      return pv_set_error(PV_ERR_TIMEOUT, "a bounded wait in the blend kernel expired (frame %llu)",
+                          (unsigned long long)v->frame);
   }
   return PV_OK;
 }

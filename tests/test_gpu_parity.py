@@ -57,6 +57,9 @@ def _check_step(spec, vol, fs, frame, kernel_tol):
 CHAIN_CASES = {
     "config1_fp32": (_spec(), 10, "noisy"),
     "ragged_fp16": (_spec(nx=3, ny=5, nz=7, rays=37, state_fmt="f16"), 5, "noisy"),
+    "ragged_k_fp16": (_spec(nx=5, ny=7, nz=9, rays=36, state_fmt="f16"), 4, "noisy"),
+    "bf16_operands": (_spec(nx=6, ny=5, nz=4, rays=64, state_fmt="f16", operand_fmt="bf16"), 3, "noisy"),
+    "f16_operands": (_spec(nx=6, ny=5, nz=4, rays=64, state_fmt="f16", operand_fmt="f16"), 3, "noisy"),
     "single_probe": (_spec(nx=1, ny=1, nz=1, rays=8), 3, "noisy"),
     "paper_tiles_10x10_18x18": (_spec(nx=4, ny=2, nz=3, rays=96, color_interior=8, vis_interior=16,
                                       state_fmt="f16"), 4, "noisy"),
