@@ -9,6 +9,8 @@ Tolerances (written here, derived in the design doc):
     given identical texels (the oracle is loaded with the GPU's texels).
 relative error = |got - ref| / max(|ref|, 1e-6 * max|ref|).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -80,7 +82,12 @@ def test_chain_step_by_step(case, kernel):
         _, exact = H.device_inputs(fs, f)
         free.step(*exact)
     tc, tv, *_ = H.gpu_state(vol)
-    if spec.state_fmt == "f32":
+    if spec.operand_fmt != "f32":
+        # 16-bit operands: the state is an average of means each within 2e-3, plus
+        # one binary16 rounding (2^-11) per stored value
+        assert H.rel_err(tc, free.tiles_c).max() <= 2e-3 + 2.0 ** -11
+        assert H.rel_err(tv, free.tiles_v).max() <= 2e-3 + 2.0 ** -11
+    elif spec.state_fmt == "f32":
         assert H.rel_err(tc, free.tiles_c).max() <= 1e-5
         assert H.rel_err(tv, free.tiles_v).max() <= 1e-5
     else:
@@ -102,8 +109,13 @@ def test_blend_mean_accuracy_full_size(operand_fmt, tol, kernel):
     m_c, m_v = blend.blend_means(*exact, 6, 14, 50.0)
     ec = H.rel_err(octahedral.interior(tc), m_c)
     ev = H.rel_err(octahedral.interior(tv), m_v)
-    print(f"\n{operand_fmt}/{vol.kernel}: colour max {ec.max():.3e} mean {ec.mean():.3e}; "
-          f"visibility max {ev.max():.3e} mean {ev.mean():.3e}")
+    line = (f"{operand_fmt}/{vol.kernel}: colour max {ec.max():.3e} mean {ec.mean():.3e}; "
+            f"visibility max {ev.max():.3e} mean {ev.mean():.3e}")
+    print("\n" + line)
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "accuracy.txt"), "a") as f:
+            f.write(line + "\n")
     assert ec.max() <= tol
     assert ev.max() <= tol
     vol.close()
