@@ -25,16 +25,17 @@
 //        TF32 parts, three MMAs (hi*hi + hi*lo + lo*hi) recover float32
 //        accuracy.
 //
-// Warp roles (256 threads, one CTA per SM, persistent over work items):
+// Warp roles (384 threads, one CTA per SM, persistent over work items):
 //   warp 0     TMA producer: ray tiles and weight tiles into a ring of stages;
 //              the item's old texels and last-transmitted codes (bulk copies)
 //   warp 1     TMEM allocation and the single MMA-issuing thread
 //   warps 2-3  converters: d^2 rows, TF32 hi/lo split
-//   warps 4-7  epilogue: TMEM -> registers -> shared (transposed), then the
-//              fused per-texel work of Sections 3.2-3.4 (weight-sum division,
-//              hysteresis, storage rounding, guard band, transmitted code,
-//              comparison with the last-transmitted code, changed flags) on the
-//              item's tiles in shared memory, written back by bulk copies.
+//   warps 4-11 epilogue: TMEM -> registers -> shared (transposed), then the
+//              fused per-texel work of Sections 3.2-3.4 (weight-sum
+//              normalisation, hysteresis, storage rounding, guard band,
+//              transmitted code, comparison with the last-transmitted code,
+//              changed flags) on the item's tiles in shared memory, one probe
+//              row per warp and one texel per lane, written back by bulk copies.
 // Accumulators are double-buffered in TMEM when both fit in 256 columns, so
 // an item's epilogue overlaps the next item's MMAs. Every mbarrier wait is
 // bounded in time; on expiry the kernel raises the volume's error word and
@@ -53,7 +54,8 @@ namespace {
 
 enum Form { kF16 = 0, kBF16 = 1, kF32 = 2 };
 
-constexpr int NT = 256;
+constexpr int NT = 384;
+constexpr int EPI_THREADS = 256;         // warps 4..11
 constexpr int ROWB = 64;                 // bytes per K-chunk row in shared memory
 constexpr int GRP = 32;                  // rows per row group of the A tile
 constexpr int MS_LD = 129;               // odd leading dimension of the transpose buffer
@@ -66,7 +68,7 @@ struct TcParams {
   int crow;                              // first A row of the colour block
   int a_rows;                            // rows of the A tile
   int off_a_lo, off_wc, off_wc_lo, off_wv, off_wv_lo, stage_bytes;
-  int off_state, off_last, off_ms, off_invs, off_flags, off_bar;
+  int off_state, off_last, off_ms, off_invs, off_flags, off_bar, off_tab;
   uint32_t stage_tx;
   uint32_t idesc_c, idesc_v;
 };
@@ -119,7 +121,7 @@ __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 2, 64;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -199,25 +201,32 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
 }
 
 // ------------------------------------------------------------------ epilogue texel
-// One texel of one probe row, on the item's tiles in shared memory: returns
-// whether its transmitted code differs from the last-transmitted one.
-__device__ __forceinline__ bool update_texel(void* tiles, size_t tile_off, int n, int t, float acc, float S,
-                                             float h, float omh, const pv_dev& k, bool vis,
-                                             uint32_t last) {
-  const int tile = n + 2, i = t / n, j = t % n;
-  const size_t at = tile_off + (size_t)(i + 1) * tile + (j + 1);
-  uint32_t bits = pv::load_state_bits(tiles, at, k.state_fmt);
-  if (S > 0.0f) {
-    const float m = acc / S;
-    const float old = pv::state_value_of_bits(bits, k.state_fmt);
-    bits = pv::state_bits_of(fmaf(h, old, omh * m), k.state_fmt);
-    pv::store_state_bits(tiles, at, bits, k.state_fmt);
-  }
+// Per-texel constants of the epilogue, built once per launch: the texel's
+// position in its tile and the guard-band positions that copy it (at most
+// three for n >= 2, packed 16 bits each, count in the top 16 bits).
+__device__ __forceinline__ uint64_t pack_border(int i, int j, int n) {
   int tr[8], tc[8];
   const int nb = pv::border_targets(i, j, n, tr, tc);
-  for (int b = 0; b < nb; ++b) pv::store_state_bits(tiles, tile_off + (size_t)tr[b] * tile + tc[b], bits, k.state_fmt);
-  const uint32_t code = vis ? pv::vis_code_of_bits(bits, k.state_fmt)
-                            : pv::color_code_of_bits(bits, k.state_fmt, k.color_code);
+  uint64_t v = 0;
+  int m = nb < 3 ? nb : 3;
+  for (int b = 0; b < m; ++b) v |= (uint64_t)(tr[b] * (n + 2) + tc[b]) << (16 * b);
+  return v | ((uint64_t)m << 48);
+}
+
+// One texel of one probe row on the item's tiles in shared memory. rS is
+// 1/sum(W) (0 when the texel has no weight: it keeps its value). Returns
+// whether the transmitted code differs from the last-transmitted one.
+__device__ __forceinline__ bool texel_update(void* tiles, uint32_t pos, uint64_t border, float acc, float rS,
+                                             float h, float omh, int fmt, bool vis, int kind, uint32_t last) {
+  uint32_t bits = pv::load_state_bits(tiles, pos, fmt);
+  if (rS > 0.0f) {
+    const float old = pv::state_value_of_bits(bits, fmt);
+    bits = pv::state_bits_of(fmaf(h, old, omh * (acc * rS)), fmt);
+    pv::store_state_bits(tiles, pos, bits, fmt);
+  }
+  const int nb = (int)(border >> 48);
+  for (int b = 0; b < nb; ++b) pv::store_state_bits(tiles, (uint32_t)(border >> (16 * b)) & 0xFFFFu, bits, fmt);
+  const uint32_t code = vis ? pv::vis_code_of_bits(bits, fmt) : pv::color_code_of_bits(bits, fmt, kind);
   return code != last;
 }
 
@@ -263,11 +272,13 @@ __global__ void __launch_bounds__(NT, 1)
   uint64_t* tempty = tfull + 2;                    // [2]
   uint64_t* efull = tempty + 2;                    // [1]: an item's texels and codes arrived
   uint32_t* tmem_holder = (uint32_t*)(efull + 1);
-  float* wsum = (float*)(smem + tp.off_invs);      // [Nc + Nv]: weight sums
+  float* rsum = (float*)(smem + tp.off_invs);      // [Nc + Nv]: 1 / weight sum (0: no weight)
+  uint64_t* tab_border = (uint64_t*)(smem + tp.off_tab);           // [Tc + Tv]
+  uint16_t* tab_pos = (uint16_t*)(tab_border + k.Tc + k.Tv);       // [Tc + Tv]
   int* flag_s = (int*)(smem + tp.off_flags);       // [5][32]
   uint8_t* state_s = smem + tp.off_state;
   uint16_t* last_s = (uint16_t*)(smem + tp.off_last);
-  float* ms = (float*)(smem + tp.off_ms);          // [32][MS_LD]
+  float* ms = (float*)(smem + tp.off_ms);          // [32][MS_LD]: accumulators, transposed
 
   const int sb = k.state_fmt == PV_FMT_F16 ? 2 : 4;
   const int np = tp.np;
@@ -285,14 +296,19 @@ __global__ void __launch_bounds__(NT, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], EPI_THREADS);
     }
     mbar_init(efull, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int t = threadIdx.x; t < k.Tc + k.Tv; t += NT) {
     const bool vis = t >= k.Tc;
-    wsum[vis ? tp.Nc + (t - k.Tc) : t] = k.sums[t];
+    const float S = k.sums[t];
+    rsum[vis ? tp.Nc + (t - k.Tc) : t] = S > 0.0f ? 1.0f / S : 0.0f;
+    const int n = vis ? k.nv : k.nc, tt = vis ? t - k.Tc : t;
+    const int i = tt / n, j = tt % n;
+    tab_pos[t] = (uint16_t)((i + 1) * (n + 2) + (j + 1));
+    tab_border[t] = pack_border(i, j, n);
   }
   for (int q = threadIdx.x; q < 5 * GRP; q += NT) flag_s[q] = 0;
   if (warp == 1) {
@@ -465,11 +481,14 @@ __global__ void __launch_bounds__(NT, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int e = threadIdx.x - 128;                   // 0..127 = TMEM lane
-    const int quarter = warp & 3;                      // lanes 32*quarter .. +32
+    const int e = threadIdx.x - 128;                   // 0..255
+    const int ew = e >> 5;                             // epilogue warp 0..7
+    const int quarter = warp & 3;                      // TMEM lanes 32*quarter .. +32
+    const int half = ew >> 2;                          // which 16-column half of a pass it loads
     const float h = *k.hy, omh = 1.0f - h;
     const float d2_scale = FORM == kF16 ? 256.0f : 1.0f;
     const bool d2_lo = FORM != kF32;                   // d^2 lo rows at lanes 64..95
+    const int fmt = k.state_fmt, kind = k.color_code;
     int b = 0;
     uint32_t tph = 0, eph = 0;
     bool ok = true;
@@ -490,37 +509,44 @@ __global__ void __launch_bounds__(NT, 1)
         const bool vis = pass >= npass_c;
         const int blk = vis ? pass - npass_c : pass;
         const int N = vis ? tp.Nv : tp.Nc;
-        const int col = (vis ? tp.col_v : tp.col_c) + 32 * blk;
-        const int ncols = min(32, N - 32 * blk);
-        float v[32];
-        tmem_ld16(trow + col, v);
-        if (ncols > 16) tmem_ld16(trow + col + 16, v + 16);
-        tmem_wait_ld();
-        for (int j = 0; j < ncols; ++j) ms[j * MS_LD + e] = v[j];
+        const int c16 = 32 * blk + 16 * half;          // first of the 16 columns this warp loads
+        if (c16 < N) {
+          float v[16];
+          tmem_ld16(trow + (vis ? tp.col_v : tp.col_c) + c16, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) ms[(16 * half + j) * MS_LD + quarter * 32 + lane] = v[j];
+        }
         epi_bar();
+        // lane <-> texel t of this pass; constants of that texel
         const int T = vis ? k.Tv : k.Tc;
-        const int tn = min(32, T - 32 * blk);
-        const int nch = vis ? 2 : 3;
-        const int count = nch * npi * tn;
-        for (int q = e; q < count; q += 128) {
-          const int tt = q % tn, rest = q / tn;
-          const int p = rest % npi, ch = rest / npi;
-          const int t = 32 * blk + tt;
-          float acc;
-          if (vis) {
-            acc = ch == 0 ? ms[tt * MS_LD + p] : ms[tt * MS_LD + 32 + p];
-            if (ch == 1 && d2_lo) acc += ms[tt * MS_LD + 64 + p];
-            if (ch == 1) acc *= d2_scale;
-          } else {
-            acc = ms[tt * MS_LD + 32 + ch * GRP + p];
+        const int t = 32 * blk + lane;
+        const bool has_t = t < T;
+        const int tg = has_t ? (vis ? k.Tc + t : t) : 0;
+        const uint32_t pos = tab_pos[tg];
+        const uint64_t bord = tab_border[tg];
+        const float rS = has_t ? rsum[(vis ? tp.Nc : 0) + t] : 0.0f;
+        const float* mcol = ms + lane * MS_LD;
+        const int rows = (vis ? 2 : 3) * npi;
+        for (int rr = ew; rr < rows; rr += 8) {
+          const int ch = rr >= npi ? (rr >= 2 * npi ? 2 : 1) : 0;
+          const int p = rr - ch * npi;
+          bool changed = false;
+          if (has_t) {
+            if (vis) {
+              float acc = ch == 0 ? mcol[p] : mcol[32 + p];
+              if (ch == 1) acc = (acc + (d2_lo ? mcol[64 + p] : 0.0f)) * d2_scale;
+              void* tiles = st_v + ((size_t)ch * np + p) * k.sv_stride * sb;
+              const uint32_t last = ls_v[((size_t)ch * np + p) * k.lv_stride + t];
+              changed = texel_update(tiles, pos, bord, acc, rS, h, omh, fmt, true, kind, last);
+            } else {
+              const float acc = mcol[32 + ch * GRP + p];
+              void* tiles = st_c + ((size_t)ch * np + p) * k.sc_stride * sb;
+              const uint32_t last = ls_c[((size_t)ch * np + p) * k.lc_stride + t];
+              changed = texel_update(tiles, pos, bord, acc, rS, h, omh, fmt, false, kind, last);
+            }
           }
-          const float S = wsum[(vis ? tp.Nc : 0) + t];
-          void* tiles = vis ? (void*)st_v : (void*)st_c;
-          const size_t toff = ((size_t)ch * np + p) * (vis ? k.sv_stride : k.sc_stride);
-          const uint32_t last = vis ? ls_v[((size_t)ch * np + p) * k.lv_stride + t]
-                                    : ls_c[((size_t)ch * np + p) * k.lc_stride + t];
-          if (update_texel(tiles, toff, vis ? k.nv : k.nc, t, acc, S, h, omh, k, vis, last))
-            atomicOr(&flag_s[((vis ? 3 : 0) + ch) * GRP + p], 1);
+          if (__any_sync(0xffffffffu, changed) && lane == 0) flag_s[((vis ? 3 : 0) + ch) * GRP + p] = 1;
         }
         epi_bar();
       }
@@ -531,7 +557,7 @@ __global__ void __launch_bounds__(NT, 1)
         b = 0;
         tph ^= 1;
       }
-      for (int q = e; q < 5 * npi; q += 128) {
+      for (int q = e; q < 5 * npi; q += EPI_THREADS) {
         const int ch5 = q / npi, p = q % npi;
         k.flags[(size_t)ch5 * k.P + p0 + p] = (uint8_t)flag_s[ch5 * GRP + p];
         flag_s[ch5 * GRP + p] = 0;
@@ -616,6 +642,10 @@ bool pv_tc_supported(const pv_desc* d, const char** why) {
   const int ob = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
   const int nc = d->color_interior, nv = d->vis_interior;
   const int Nc = ((nc * nc + 15) / 16) * 16, Nv = ((nv * nv + 15) / 16) * 16;
+  if (nc < 2 || nv < 2) {
+    if (why) *why = "tile interiors below 2x2 (guard-band table holds three copies per texel)";
+    return false;
+  }
   if ((d->rays_per_probe * ob) % 16 != 0) {
     if (why) *why = "rays_per_probe * operand bytes must be a multiple of 16 (TMA row pitch)";
     return false;
@@ -686,8 +716,9 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   // epilogue region
   const size_t epi_state = (size_t)np * (3 * k.sc_stride + 2 * k.sv_stride) * sb;
   const size_t epi_last = (size_t)np * (3 * k.lc_stride + 2 * k.lv_stride) * 2;
+  const size_t tab = (size_t)(k.Tc + k.Tv) * 10;
   const size_t epi = align1k(epi_state) + align1k(epi_last) + align1k((size_t)32 * MS_LD * 4) +
-                     align1k((size_t)(tp.Nc + tp.Nv) * 4) + align1k(5 * GRP * 4) + 1024;
+                     align1k((size_t)(tp.Nc + tp.Nv) * 4) + align1k(5 * GRP * 4) + align1k(tab) + 1024;
   const size_t budget = (size_t)smem_max - 1024 - epi;
   int stages = (int)(budget / tp.stage_bytes);
   if (stages > 4) stages = 4;
@@ -707,6 +738,8 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   off += align1k((size_t)(tp.Nc + tp.Nv) * 4);
   tp.off_flags = (int)off;
   off += align1k(5 * GRP * 4);
+  tp.off_tab = (int)off;
+  off += align1k(tab);
   tp.off_bar = (int)off;
   off += 1024;
   pl->smem = off + 1024;                       // slack for aligning the dynamic base
