@@ -44,7 +44,7 @@ struct Layout {
   int sc_stride, sv_stride, lc_stride, lv_stride;
   size_t off_state_c, off_state_v, off_last_c, off_last_v, off_flags, off_wrt, off_sums, off_wop,
       off_hy, off_frame, off_idx_c, off_idx_v, off_delta_c, off_delta_v, off_counts, off_planes_c,
-      off_planes_v, off_err, total;
+      off_planes_v, off_err, off_sel, total;
 };
 
 pv_status validate(const pv_desc* d) {
@@ -130,6 +130,7 @@ Layout layout_of(const pv_desc* d) {
   L.off_delta_c = take((size_t)L.P * 2);
   L.off_delta_v = take((size_t)L.P * 2);
   L.off_counts = take(16);
+  L.off_sel = take(64);
   L.off_planes_c = take((size_t)3 * L.cheight * L.cpitch);
   L.off_planes_v = take((size_t)3 * L.vheight * L.vpitch);
   L.off_err = take(16);
@@ -239,6 +240,8 @@ pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
   k.delta_c = (uint16_t*)(b + L.off_delta_c);
   k.delta_v = (uint16_t*)(b + L.off_delta_v);
   k.counts = (uint32_t*)(b + L.off_counts);
+  k.sel = (uint32_t*)(b + L.off_sel);
+  k.sel_frame = (unsigned long long*)(b + L.off_sel + 32);
   k.planes_c = (uint16_t*)(b + L.off_planes_c);
   k.planes_v = (uint8_t*)(b + L.off_planes_v);
   k.tc_pad = L.tc_pad; k.tv_pad = L.tv_pad; k.r_pad = L.r_pad;
@@ -250,6 +253,10 @@ pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
   e = cudaMemset(v->base, 0, L.total);
   if (e == cudaSuccess) e = cudaMemset(k.last_c, 0xFF, (size_t)3 * L.P * L.lc_stride * 2);
   if (e == cudaSuccess) e = cudaMemset(k.last_v, 0xFF, (size_t)2 * L.P * L.lv_stride * 2);
+  if (e == cudaSuccess) {
+    const unsigned long long never = ~0ull;           // no select yet: flags are fresh
+    e = cudaMemcpy(k.sel_frame, &never, sizeof never, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = pv_simt_prepare();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess && kernel == PV_KERNEL_TCGEN05) e = pv_tc_plan_create(v);
@@ -331,9 +338,8 @@ pv_status probe_select_and_pack(pv_volume* v, pv_frame* out, int32_t want_host_c
   if (!v || !out) return pv_set_error(PV_ERR_INVALID, "probe_select_and_pack: NULL argument");
   DeviceGuard g(v->device);
   cudaStream_t st = as_stream(stream);
-  cudaError_t e = pv_launch_select(v->k, st);
-  if (e == cudaSuccess) e = pv_launch_pack(v->k, st);
-  if (e != cudaSuccess) return cuda_fail(e, "select/pack kernels");
+  cudaError_t e = pv_launch_select_pack(v->k, st);
+  if (e != cudaSuccess) return cuda_fail(e, "select/pack kernel");
   out->color_planes = v->k.planes_c;
   out->vis_planes = v->k.planes_v;
   out->index_c = v->k.idx_c;
@@ -464,7 +470,9 @@ pv_status probe_volume_import_state(pv_volume* v, const void* tiles_c, const voi
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(k.last_v, (size_t)k.lv_stride * 2, last_v, (size_t)k.Tv * 2,
                           (size_t)k.Tv * 2, (size_t)2 * k.P, cudaMemcpyDefault, st);
+  static const unsigned long long never = ~0ull;      // imported flags count as fresh
   if (e == cudaSuccess) e = cudaMemcpyAsync(k.frame, &f, sizeof f, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(k.sel_frame, &never, sizeof never, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = pv_launch_recompute_flags(k, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "import");

@@ -213,21 +213,87 @@ __device__ __forceinline__ uint64_t pack_border(int i, int j, int n) {
   return v | ((uint64_t)m << 48);
 }
 
-// One texel of one probe row on the item's tiles in shared memory. rS is
-// 1/sum(W) (0 when the texel has no weight: it keeps its value). Returns
-// whether the transmitted code differs from the last-transmitted one.
-__device__ __forceinline__ bool texel_update(void* tiles, uint32_t pos, uint64_t border, float acc, float rS,
-                                             float h, float omh, int fmt, bool vis, int kind, uint32_t last) {
-  uint32_t bits = pv::load_state_bits(tiles, pos, fmt);
-  if (rS > 0.0f) {
-    const float old = pv::state_value_of_bits(bits, fmt);
-    bits = pv::state_bits_of(fmaf(h, old, omh * (acc * rS)), fmt);
-    pv::store_state_bits(tiles, pos, bits, fmt);
+__device__ __forceinline__ uint32_t lds16(uint32_t a) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts16(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v) : "memory");
+}
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// State format as a compile-time choice: 0 binary16, 1 binary32.
+template <int SF>
+struct StateOps {
+  static __device__ __forceinline__ uint32_t load(uint32_t a) { return SF == 0 ? lds16(a) : lds32(a); }
+  static __device__ __forceinline__ void store(uint32_t a, uint32_t b) {
+    if (SF == 0) sts16(a, b);
+    else sts32(a, b);
   }
-  const int nb = (int)(border >> 48);
-  for (int b = 0; b < nb; ++b) pv::store_state_bits(tiles, (uint32_t)(border >> (16 * b)) & 0xFFFFu, bits, fmt);
-  const uint32_t code = vis ? pv::vis_code_of_bits(bits, fmt) : pv::color_code_of_bits(bits, fmt, kind);
-  return code != last;
+  static __device__ __forceinline__ float value(uint32_t b) {
+    return SF == 0 ? __half2float(__ushort_as_half((unsigned short)b)) : __uint_as_float(b);
+  }
+  static __device__ __forceinline__ uint32_t bits(float v) {
+    return SF == 0 ? (uint32_t)__half_as_ushort(__float2half_rn(v)) : __float_as_uint(v);
+  }
+};
+
+// Per-lane constants of the texel a lane handles in an epilogue pass.
+struct LaneTexel {
+  bool has;
+  uint32_t pos, b0, b1, b2;   // byte offsets in the tile: texel and its guard-band copies
+  int nb;
+  float rS;                   // 1 / weight sum (0: no weight, the texel keeps its value)
+  uint32_t t2;                // byte offset of the texel's code in a code row
+};
+
+// One pass of the fused epilogue: every probe row (ch, p) of this texture, one
+// warp per row and one texel per lane. The shared tiles are updated in place
+// (weight-sum normalisation, hysteresis, storage rounding, guard band) and the
+// row's changed flag is raised when any transmitted code differs from the
+// last-transmitted one.
+template <int SF, int KIND, bool VIS, bool D2LO>
+__device__ __forceinline__ void epi_rows(const LaneTexel& lt, const float* mcol, int rows, int npi, int np,
+                                         uint32_t tiles, uint32_t tile_bytes, uint32_t codes, uint32_t code_bytes,
+                                         float h, float omh, float d2_scale, int ew, int lane, int* flag_s) {
+  for (int rr = ew; rr < rows; rr += 8) {
+    const int ch = rr >= npi ? (rr >= 2 * npi ? 2 : 1) : 0;
+    const int p = rr - ch * npi;
+    const uint32_t tile = tiles + (uint32_t)(ch * np + p) * tile_bytes;
+    const uint32_t code_row = codes + (uint32_t)(ch * np + p) * code_bytes;
+    bool changed = false;
+    if (lt.has) {
+      float acc;
+      if (VIS) {
+        acc = ch == 0 ? mcol[p] : mcol[32 + p];
+        if (ch == 1) acc = (D2LO ? acc + mcol[64 + p] : acc) * d2_scale;
+      } else {
+        acc = mcol[32 + 32 * ch + p];
+      }
+      uint32_t b = StateOps<SF>::load(tile + lt.pos);
+      if (lt.rS > 0.0f) {
+        b = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(b), omh * (acc * lt.rS)));
+        StateOps<SF>::store(tile + lt.pos, b);
+      }
+      if (lt.nb > 0) StateOps<SF>::store(tile + lt.b0, b);
+      if (lt.nb > 1) StateOps<SF>::store(tile + lt.b1, b);
+      if (lt.nb > 2) StateOps<SF>::store(tile + lt.b2, b);
+      uint32_t code;
+      if (VIS) code = SF == 0 ? b : (uint32_t)__half_as_ushort(__float2half_rn(__uint_as_float(b)));
+      else if (KIND == PV_CODE_UNORM10) code = pv::unorm10_from_float(StateOps<SF>::value(b));
+      else code = SF == 0 ? pv::uf10_from_half_bits(b) : pv::uf10_from_float_bits(b);
+      changed = code != lds16(code_row + lt.t2);
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) flag_s[((VIS ? 3 : 0) + ch) * GRP + p] = 1;
+  }
 }
 
 // The item's old texels and last-transmitted codes, into shared memory.
@@ -262,7 +328,6 @@ __global__ void __launch_bounds__(NT, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool kSplitW = FORM != kF16;
   constexpr bool kSplitA = FORM == kF32;
-  constexpr int kBytes = FORM == kF32 ? 4 : 2;
 
   uint64_t* bars = (uint64_t*)(smem + tp.off_bar);
   uint64_t* full = bars;                           // [stages]
@@ -487,8 +552,8 @@ __global__ void __launch_bounds__(NT, 1)
     const int half = ew >> 2;                          // which 16-column half of a pass it loads
     const float h = *k.hy, omh = 1.0f - h;
     const float d2_scale = FORM == kF16 ? 256.0f : 1.0f;
-    const bool d2_lo = FORM != kF32;                   // d^2 lo rows at lanes 64..95
-    const int fmt = k.state_fmt, kind = k.color_code;
+    constexpr bool d2_lo = FORM != kF32;               // d^2 lo rows at lanes 64..95
+    const int kind = k.color_code;
     int b = 0;
     uint32_t tph = 0, eph = 0;
     bool ok = true;
@@ -521,32 +586,33 @@ __global__ void __launch_bounds__(NT, 1)
         // lane <-> texel t of this pass; constants of that texel
         const int T = vis ? k.Tv : k.Tc;
         const int t = 32 * blk + lane;
-        const bool has_t = t < T;
-        const int tg = has_t ? (vis ? k.Tc + t : t) : 0;
-        const uint32_t pos = tab_pos[tg];
+        LaneTexel lt;
+        lt.has = t < T;
+        const int tg = lt.has ? (vis ? k.Tc + t : t) : 0;
         const uint64_t bord = tab_border[tg];
-        const float rS = has_t ? rsum[(vis ? tp.Nc : 0) + t] : 0.0f;
+        lt.pos = (uint32_t)tab_pos[tg] * sb;
+        lt.nb = (int)(bord >> 48);
+        lt.b0 = (uint32_t)(bord & 0xFFFFu) * sb;
+        lt.b1 = (uint32_t)((bord >> 16) & 0xFFFFu) * sb;
+        lt.b2 = (uint32_t)((bord >> 32) & 0xFFFFu) * sb;
+        lt.rS = lt.has ? rsum[(vis ? tp.Nc : 0) + t] : 0.0f;
+        lt.t2 = (uint32_t)t * 2;
         const float* mcol = ms + lane * MS_LD;
         const int rows = (vis ? 2 : 3) * npi;
-        for (int rr = ew; rr < rows; rr += 8) {
-          const int ch = rr >= npi ? (rr >= 2 * npi ? 2 : 1) : 0;
-          const int p = rr - ch * npi;
-          bool changed = false;
-          if (has_t) {
-            if (vis) {
-              float acc = ch == 0 ? mcol[p] : mcol[32 + p];
-              if (ch == 1) acc = (acc + (d2_lo ? mcol[64 + p] : 0.0f)) * d2_scale;
-              void* tiles = st_v + ((size_t)ch * np + p) * k.sv_stride * sb;
-              const uint32_t last = ls_v[((size_t)ch * np + p) * k.lv_stride + t];
-              changed = texel_update(tiles, pos, bord, acc, rS, h, omh, fmt, true, kind, last);
-            } else {
-              const float acc = mcol[32 + ch * GRP + p];
-              void* tiles = st_c + ((size_t)ch * np + p) * k.sc_stride * sb;
-              const uint32_t last = ls_c[((size_t)ch * np + p) * k.lc_stride + t];
-              changed = texel_update(tiles, pos, bord, acc, rS, h, omh, fmt, false, kind, last);
-            }
-          }
-          if (__any_sync(0xffffffffu, changed) && lane == 0) flag_s[((vis ? 3 : 0) + ch) * GRP + p] = 1;
+        const uint32_t tiles = smem_u32(vis ? st_v : st_c);
+        const uint32_t tile_bytes = (uint32_t)(vis ? k.sv_stride : k.sc_stride) * sb;
+        const uint32_t codes = smem_u32(vis ? ls_v : ls_c);
+        const uint32_t code_bytes = (uint32_t)(vis ? k.lv_stride : k.lc_stride) * 2;
+        const bool f16 = k.state_fmt == PV_FMT_F16;
+        if (vis) {
+          if (f16) epi_rows<0, 0, true, d2_lo>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, d2_scale, ew, lane, flag_s);
+          else epi_rows<1, 0, true, d2_lo>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, d2_scale, ew, lane, flag_s);
+        } else if (kind == PV_CODE_UNORM10) {
+          if (f16) epi_rows<0, PV_CODE_UNORM10, false, false>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, 1.0f, ew, lane, flag_s);
+          else epi_rows<1, PV_CODE_UNORM10, false, false>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, 1.0f, ew, lane, flag_s);
+        } else {
+          if (f16) epi_rows<0, PV_CODE_UF10, false, false>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, 1.0f, ew, lane, flag_s);
+          else epi_rows<1, PV_CODE_UF10, false, false>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, 1.0f, ew, lane, flag_s);
         }
         epi_bar();
       }

@@ -34,7 +34,10 @@ struct pv_dev {
   uint16_t* idx_v;
   uint16_t* delta_c;
   uint16_t* delta_v;
-  uint32_t* counts;                     // [4]: count_c, count_v, prev_c, prev_v
+  uint32_t* counts;                     // [2]: count_c, count_v of the last packed frame
+  uint32_t* sel;                        // [8]: select sequence, finished-CTA ticket, counts
+                                        // history by sequence parity ([2 + 2*par] c, [3 + 2*par] v)
+  unsigned long long* sel_frame;        // [1]: frame counter value at the last select
   uint16_t* planes_c;                   // 3 planes of ch rows x cpitch bytes
   uint8_t* planes_v;                    // 3 planes of vh rows x vpitch bytes
   int tc_pad, tv_pad, r_pad;            // padded shapes of w_op
@@ -66,8 +69,7 @@ cudaError_t pv_launch_weights(const pv_dev& k, const float* dirs, int want_rt, i
 cudaError_t pv_simt_prepare();
 cudaError_t pv_launch_blend_simt(const pv_dev& k, const void* rad, const void* dist,
                                  cudaStream_t s);
-cudaError_t pv_launch_select(const pv_dev& k, cudaStream_t s);
-cudaError_t pv_launch_pack(const pv_dev& k, cudaStream_t s);
+cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t s);
 cudaError_t pv_launch_recompute_flags(const pv_dev& k, cudaStream_t s);
 
 // tensor-core blend (pv_blend_tc.cu)

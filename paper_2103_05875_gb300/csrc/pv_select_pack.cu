@@ -1,160 +1,200 @@
-// K2-K4: change selection, probe index buffers and bit packing (Sections 3.3
-// and 3.4 of arXiv 2103.05875), plus the flag recomputation used after a
-// state import.
+// Change selection, probe index buffers and bit packing (Sections 3.3 and
+// 3.4 of arXiv 2103.05875), fused into one kernel, plus the flag
+// recomputation used after a state import.
 //
-// K2 (select): one block per texture (colour, visibility). Each probe's
-//   changed flag is the OR of its channel flags written by the blend
-//   epilogue; a block-wide exclusive scan in ascending probe id gives each
-//   selected probe its slot. Writes the uint16 index buffer, its delta
-//   encoding (d0 = id0, dk = id_k - id_(k-1)) and the counts, keeping the
-//   previous frame's count so the pack kernels can clear slots that were used
-//   last frame and are empty now.
-// K3 (colour pack): one thread per (slot, channel, interior row): the row's
-//   UF10/UNORM10 codes go to plane c at block (k / B_w, k % B_w) as 16-bit
-//   samples (code << 6 unless color_lsb), and to the last-transmitted texture.
-// K4 (visibility pack): output-centric; one thread per (atlas row, group of
-//   three RG16F texels). The twelve bytes (R.lo, R.hi, G.lo, G.hi per texel)
-//   are spread over Y, U, V as YUVY / UVYU / VYUV, i.e. one aligned 32-bit
-//   word per plane, so plane rows are written with coalesced word stores.
-// Slots at or beyond max(count, previous count) are left untouched: they are
-// already zero.
+// Selection: a probe is sent iff any of its channel flags (raised by the
+// blend when a transmitted code differs from the last-transmitted one) is
+// set; slots are assigned in ascending probe id. Every block scans all flags
+// (a few bytes per probe, from L2), so each block knows the slot of every
+// probe and the total without a grid-wide synchronisation; it then packs its
+// own contiguous range of probes, one warp per probe:
+//   colour: the 10-bit codes of the interior go to planes Y=R, U=G, V=B at
+//           block (k / B_w, k % B_w) as 16-bit samples (code << 6 unless
+//           color_lsb), and to the last-transmitted texture;
+//   visibility: per atlas row each texel's bytes (R.lo, R.hi, G.lo, G.hi)
+//           continue the row's byte stream; byte s goes to plane s mod 3,
+//           column s div 3 (the paper's YUVY / UVYU / VYUV pattern). Byte
+//           stores, because neighbouring slots share plane words.
+// Each block writes its probes' index-buffer entries and deltas
+// (d0 = id0, dk = id_k - id_(k-1)); slots that held a probe last frame but
+// are empty now are cleared (slots beyond both counts are already zero).
+// Flags count only once per update: the kernel compares the frame counter
+// with the frame of the previous select, so a second select without a new
+// update selects nothing. The last block to finish advances the select
+// sequence (which double-buffers the previous counts).
 #include "pv_codes.cuh"
 #include "pv_internal.h"
 
 namespace {
 
-constexpr int SCAN_THREADS = 1024;
+constexpr int SP_THREADS = 256;
+constexpr int SP_MAX_RANGE = 512;        // probes per block (shared slot tables)
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_select(pv_dev k) {
-  const int which = blockIdx.x;                  // 0 colour, 1 visibility
-  const int nch = which ? 2 : 3;
-  uint8_t* flags = k.flags + (size_t)(which ? 3 : 0) * k.P;
-  uint16_t* idx = which ? k.idx_v : k.idx_c;
-  uint16_t* delta = which ? k.delta_v : k.delta_c;
-  const int tid = threadIdx.x;
-  const int per = (k.P + SCAN_THREADS - 1) / SCAN_THREADS;
-  const int b = min(k.P, tid * per), e = min(k.P, b + per);
-
-  int local = 0;
-  for (int p = b; p < e; ++p) {
-    int f = 0;
-    for (int c = 0; c < nch; ++c) f |= flags[(size_t)c * k.P + p];
-    local += f != 0;
+__device__ __forceinline__ void pack_color_probe(const pv_dev& k, int p, int slot, int lane) {
+  const int by = slot / k.bw, bx = slot % k.bw;
+  const int per = 3 * k.Tc;
+  for (int q = lane; q < per; q += 32) {
+    const int c = q / k.Tc, t = q % k.Tc, i = t / k.nc, j = t % k.nc;
+    uint16_t* dst = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(k.planes_c) +
+                                                ((size_t)c * k.ch + (size_t)by * k.nc + i) * k.cpitch) +
+                    (size_t)bx * k.nc + j;
+    if (p >= 0) {
+      const size_t at = ((size_t)c * k.P + p) * k.sc_stride + (size_t)(i + 1) * k.tc + (j + 1);
+      const uint32_t code = pv::color_code_of(k.state_c, at, k.state_fmt, k.color_code);
+      *dst = (uint16_t)(code << k.color_shift);
+      k.last_c[((size_t)c * k.P + p) * k.lc_stride + t] = (uint16_t)code;
+    } else {
+      *dst = 0;
+    }
   }
-  // block exclusive scan of the per-thread counts
-  __shared__ int warp_tot[SCAN_THREADS / 32];
-  const int lane = tid & 31, wid = tid >> 5;
-  int incl = local;
+}
+
+__device__ __forceinline__ void pack_vis_probe(const pv_dev& k, int p, int slot, int lane) {
+  const int by = slot / k.bw, bx = slot % k.bw;
+  const int n = k.nv;
+  // lanes cover (row, texel) pairs; each texel contributes four stream bytes
+  for (int q = lane; q < k.Tv; q += 32) {
+    const int i = q / n, j = q % n;
+    uint32_t c0 = 0, c1 = 0;
+    if (p >= 0) {
+      const size_t off = (size_t)(i + 1) * k.tv + (j + 1);
+      c0 = pv::vis_code_of(k.state_v, (size_t)p * k.sv_stride + off, k.state_fmt);
+      c1 = pv::vis_code_of(k.state_v, ((size_t)k.P + p) * k.sv_stride + off, k.state_fmt);
+      k.last_v[(size_t)p * k.lv_stride + q] = (uint16_t)c0;
+      k.last_v[((size_t)k.P + p) * k.lv_stride + q] = (uint16_t)c1;
+    }
+    const uint32_t bytes[4] = {c0 & 0xFFu, c0 >> 8, c1 & 0xFFu, c1 >> 8};
+    const size_t y = (size_t)by * n + i;
+    const int s0 = 4 * (bx * n + j);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int sb = s0 + b;
+      const int pl = sb % 3;
+      k.planes_v[((size_t)pl * k.vh + y) * k.vpitch + (size_t)(sb / 3)] = (uint8_t)bytes[b];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range) {
+  __shared__ int warp_c[SP_THREADS / 32], warp_v[SP_THREADS / 32];
+  __shared__ int warp_lc[SP_THREADS / 32], warp_lv[SP_THREADS / 32];
+  __shared__ int slot_c[SP_MAX_RANGE], slot_v[SP_MAX_RANGE];
+  __shared__ uint16_t prev_c[SP_MAX_RANGE], prev_v[SP_MAX_RANGE];
+  __shared__ int tot_c, tot_v;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const bool fresh = *k.frame != *k.sel_frame;
+  const uint32_t seq = k.sel[0];
+  const uint32_t par = seq & 1u;
+  const int prev_cnt_c = (int)k.sel[2 + 2 * (par ^ 1u)], prev_cnt_v = (int)k.sel[3 + 2 * (par ^ 1u)];
+  const int pb = blockIdx.x * range, pe = min(k.P, pb + range);
+
+  // 1. scan of every probe's flags
+  const int per = (k.P + SP_THREADS - 1) / SP_THREADS;
+  const int b = min(k.P, tid * per), e = min(k.P, b + per);
+  int nc = 0, nv = 0, lastc = -1, lastv = -1;
+  if (fresh) {
+    for (int p = b; p < e; ++p) {
+      const int fc = k.flags[p] | k.flags[(size_t)k.P + p] | k.flags[2 * (size_t)k.P + p];
+      const int fv = k.flags[3 * (size_t)k.P + p] | k.flags[4 * (size_t)k.P + p];
+      if (fc) { ++nc; lastc = p; }
+      if (fv) { ++nv; lastv = p; }
+    }
+  }
+  int ic = nc, iv = nv, mc = lastc, mv = lastv;        // inclusive sums / running max
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
+    const int yc = __shfl_up_sync(0xffffffffu, ic, o), yv = __shfl_up_sync(0xffffffffu, iv, o);
+    const int zc = __shfl_up_sync(0xffffffffu, mc, o), zv = __shfl_up_sync(0xffffffffu, mv, o);
+    if (lane >= o) { ic += yc; iv += yv; mc = max(mc, zc); mv = max(mv, zv); }
   }
-  if (lane == 31) warp_tot[wid] = incl;
+  if (lane == 31) { warp_c[wid] = ic; warp_v[wid] = iv; warp_lc[wid] = mc; warp_lv[wid] = mv; }
   __syncthreads();
-  if (wid == 0) {
-    int v = warp_tot[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
-    }
-    warp_tot[lane] = v;                           // inclusive over warps
-  }
-  __syncthreads();
-  const int excl = incl - local + (wid ? warp_tot[wid - 1] : 0);
-  const int total = warp_tot[SCAN_THREADS / 32 - 1];
-
-  int slot = excl;
-  for (int p = b; p < e; ++p) {
-    int f = 0;
-    for (int c = 0; c < nch; ++c) f |= flags[(size_t)c * k.P + p];
-    if (f) idx[slot++] = (uint16_t)p;
-  }
-  // every changed probe is sent now, so no flag stays raised: a second
-  // select without a new update selects nothing
-  for (int p = b; p < e; ++p)
-    for (int c = 0; c < nch; ++c) flags[(size_t)c * k.P + p] = 0;
-  __syncthreads();                               // idx visible block-wide
-  for (int s = excl; s < excl + local; ++s)
-    delta[s] = (uint16_t)(s ? (int)idx[s] - (int)idx[s - 1] : (int)idx[s]);
   if (tid == 0) {
-    k.counts[2 + which] = k.counts[which];       // previous frame's count
-    k.counts[which] = (uint32_t)total;
+    int sc = 0, sv = 0, lc = -1, lv = -1;
+    for (int w = 0; w < SP_THREADS / 32; ++w) {
+      const int a = warp_c[w], bb = warp_v[w], x = warp_lc[w], y = warp_lv[w];
+      warp_c[w] = sc; warp_v[w] = sv; warp_lc[w] = lc; warp_lv[w] = lv;
+      sc += a; sv += bb; lc = max(lc, x); lv = max(lv, y);
+    }
+    tot_c = sc; tot_v = sv;
   }
-}
-
-__global__ void __launch_bounds__(256) k_pack_color(pv_dev k) {
-  const int per_slot = 3 * k.nc;
-  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int slot = (int)(item / per_slot);
-  if (slot >= k.P) return;
-  const int cnt = (int)k.counts[0], prev = (int)k.counts[2];
-  if (slot >= max(cnt, prev)) return;
-  const int rem = (int)(item % per_slot);
-  const int c = rem / k.nc, i = rem % k.nc;
-  const int by = slot / k.bw, bx = slot % k.bw;
-  uint16_t* dst = reinterpret_cast<uint16_t*>(
-      reinterpret_cast<uint8_t*>(k.planes_c) + ((size_t)c * k.ch + (size_t)by * k.nc + i) * k.cpitch) +
-      (size_t)bx * k.nc;
-  if (slot < cnt) {
-    const int p = k.idx_c[slot];
-    const size_t row0 = ((size_t)c * k.P + p) * k.sc_stride + (size_t)(i + 1) * k.tc + 1;
-    uint16_t* last = k.last_c + ((size_t)c * k.P + p) * k.lc_stride + (size_t)i * k.nc;
-    for (int j = 0; j < k.nc; ++j) {
-      const uint32_t code = pv::color_code_of(k.state_c, row0 + j, k.state_fmt, k.color_code);
-      dst[j] = (uint16_t)(code << k.color_shift);
-      last[j] = (uint16_t)code;
+  __syncthreads();
+  // exclusive prefix and last selected probe before this thread's chunk
+  int rc = warp_c[wid] + ic - nc, rv = warp_v[wid] + iv - nv;
+  const int up_c = __shfl_up_sync(0xffffffffu, mc, 1), up_v = __shfl_up_sync(0xffffffffu, mv, 1);
+  int lc = max(warp_lc[wid], lane > 0 ? up_c : -1);
+  int lv = max(warp_lv[wid], lane > 0 ? up_v : -1);
+  // 2. slots of this block's probes
+  if (fresh) {
+    for (int p = b; p < e; ++p) {
+      const int fc = k.flags[p] | k.flags[(size_t)k.P + p] | k.flags[2 * (size_t)k.P + p];
+      const int fv = k.flags[3 * (size_t)k.P + p] | k.flags[4 * (size_t)k.P + p];
+      if (p >= pb && p < pe) {
+        slot_c[p - pb] = fc ? rc : -1;
+        slot_v[p - pb] = fv ? rv : -1;
+        prev_c[p - pb] = (uint16_t)(lc < 0 ? 0 : lc);
+        prev_v[p - pb] = (uint16_t)(lv < 0 ? 0 : lv);
+      }
+      if (fc) { ++rc; lc = p; }
+      if (fv) { ++rv; lv = p; }
     }
   } else {
-    for (int j = 0; j < k.nc; ++j) dst[j] = 0;
+    for (int p = max(b, pb); p < min(e, pe); ++p) { slot_c[p - pb] = -1; slot_v[p - pb] = -1; }
+  }
+  __syncthreads();
+  const int cnt_c = tot_c, cnt_v = tot_v;
+  // 3. pack this block's selected probes, one warp per probe
+  for (int p = pb + wid; p < pe; p += SP_THREADS / 32) {
+    const int sc = slot_c[p - pb], sv = slot_v[p - pb];
+    if (sc >= 0) {
+      pack_color_probe(k, p, sc, lane);
+      if (lane == 0) { k.idx_c[sc] = (uint16_t)p; k.delta_c[sc] = (uint16_t)(p - prev_c[p - pb]); }
+    }
+    if (sv >= 0) {
+      pack_vis_probe(k, p, sv, lane);
+      if (lane == 0) { k.idx_v[sv] = (uint16_t)p; k.delta_v[sv] = (uint16_t)(p - prev_v[p - pb]); }
+    }
+  }
+  // 4. clear slots used by the previous frame and empty now
+  for (int s = cnt_c + blockIdx.x * (SP_THREADS / 32) + wid; s < prev_cnt_c; s += gridDim.x * (SP_THREADS / 32))
+    pack_color_probe(k, -1, s, lane);
+  for (int s = cnt_v + blockIdx.x * (SP_THREADS / 32) + wid; s < prev_cnt_v; s += gridDim.x * (SP_THREADS / 32))
+    pack_vis_probe(k, -1, s, lane);
+  // 5. counts, and the select sequence once every block is done
+  if (blockIdx.x == 0 && tid == 0) {
+    k.counts[0] = (uint32_t)cnt_c;
+    k.counts[1] = (uint32_t)cnt_v;
+    k.sel[2 + 2 * par] = (uint32_t)cnt_c;
+    k.sel[3 + 2 * par] = (uint32_t)cnt_v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const uint32_t ticket = atomicAdd(&k.sel[1], 1u);
+    if (ticket == gridDim.x - 1) {
+      k.sel[1] = 0;
+      k.sel[0] = seq + 1u;
+      *k.sel_frame = *k.frame;
+      __threadfence();
+    }
   }
 }
 
-__global__ void __launch_bounds__(256) k_pack_vis(pv_dev k) {
-  const int W = k.bw * k.nv;                     // atlas width in texels
-  const int U = (W + 2) / 3;                     // groups of three texels per row
-  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= (long long)k.vh * U) return;
-  const int y = (int)(item / U), u = (int)(item % U);
-  const int by = y / k.nv, i = y % k.nv;
-  const int cnt = (int)k.counts[1], prev = (int)k.counts[3];
-  const int lim = max(cnt, prev);
-  uint32_t bytes[12];
-  bool touched = false;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-    const int t = 3 * u + q;
-    if (t < W) {
-      const int bx = t / k.nv, j = t % k.nv;
-      const int slot = by * k.bw + bx;
-      if (slot < lim) touched = true;
-      if (slot < cnt) {
-        const int p = k.idx_v[slot];
-        const size_t off = (size_t)(i + 1) * k.tv + (j + 1);
-        const size_t at0 = (size_t)p * k.sv_stride + off;
-        const size_t at1 = ((size_t)k.P + p) * k.sv_stride + off;
-        const uint32_t c0 = pv::vis_code_of(k.state_v, at0, k.state_fmt);
-        const uint32_t c1 = pv::vis_code_of(k.state_v, at1, k.state_fmt);
-        k.last_v[(size_t)p * k.lv_stride + (size_t)i * k.nv + j] = (uint16_t)c0;
-        k.last_v[((size_t)k.P + p) * k.lv_stride + (size_t)i * k.nv + j] = (uint16_t)c1;
-        lo0 = c0 & 0xFFu; hi0 = c0 >> 8; lo1 = c1 & 0xFFu; hi1 = c1 >> 8;
-      }
-    }
-    bytes[4 * q + 0] = lo0;
-    bytes[4 * q + 1] = hi0;
-    bytes[4 * q + 2] = lo1;
-    bytes[4 * q + 3] = hi1;
-  }
-  if (!touched) return;
-#pragma unroll
-  for (int pl = 0; pl < 3; ++pl) {
-    const uint32_t word = bytes[pl] | (bytes[pl + 3] << 8) | (bytes[pl + 6] << 16) | (bytes[pl + 9] << 24);
-    uint8_t* row = k.planes_v + ((size_t)pl * k.vh + y) * k.vpitch;
-    reinterpret_cast<uint32_t*>(row)[u] = word;
-  }
+}  // namespace
+
+cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t st) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int range = (k.P + sms - 1) / sms;
+  if (range < 8) range = 8;
+  if (range > SP_MAX_RANGE) range = SP_MAX_RANGE;
+  const int blocks = (k.P + range - 1) / range;
+  k_select_pack<<<blocks, SP_THREADS, 0, st>>>(k, range);
+  return cudaGetLastError();
 }
+
+namespace {
 
 // After a state import: recompute every (channel, probe) changed flag.
 __global__ void __launch_bounds__(256) k_recompute_flags(pv_dev k) {
@@ -178,20 +218,6 @@ __global__ void __launch_bounds__(256) k_recompute_flags(pv_dev k) {
 }
 
 }  // namespace
-
-cudaError_t pv_launch_select(const pv_dev& k, cudaStream_t st) {
-  k_select<<<2, SCAN_THREADS, 0, st>>>(k);
-  return cudaGetLastError();
-}
-
-cudaError_t pv_launch_pack(const pv_dev& k, cudaStream_t st) {
-  const long long items_c = (long long)k.P * 3 * k.nc;
-  k_pack_color<<<(unsigned)((items_c + 255) / 256), 256, 0, st>>>(k);
-  const int W = k.bw * k.nv;
-  const long long items_v = (long long)k.vh * ((W + 2) / 3);
-  k_pack_vis<<<(unsigned)((items_v + 255) / 256), 256, 0, st>>>(k);
-  return cudaGetLastError();
-}
 
 cudaError_t pv_launch_recompute_flags(const pv_dev& k, cudaStream_t st) {
   const long long items = 5LL * k.P;
