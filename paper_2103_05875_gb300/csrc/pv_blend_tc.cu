@@ -95,7 +95,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000000;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(smem_u32(b)), "r"(parity)
@@ -264,35 +264,57 @@ template <int SF, int KIND, bool VIS, bool D2LO>
 __device__ __forceinline__ void epi_rows(const LaneTexel& lt, const float* mcol, int rows, int npi, int np,
                                          uint32_t tiles, uint32_t tile_bytes, uint32_t codes, uint32_t code_bytes,
                                          float h, float omh, float d2_scale, int ew, int lane, int* flag_s) {
-  for (int rr = ew; rr < rows; rr += 8) {
-    const int ch = rr >= npi ? (rr >= 2 * npi ? 2 : 1) : 0;
-    const int p = rr - ch * npi;
-    const uint32_t tile = tiles + (uint32_t)(ch * np + p) * tile_bytes;
-    const uint32_t code_row = codes + (uint32_t)(ch * np + p) * code_bytes;
-    bool changed = false;
-    if (lt.has) {
-      float acc;
+  constexpr int U = 4;                                 // independent rows per warp iteration
+  for (int r0 = ew; r0 < rows; r0 += 8 * U) {
+    uint32_t tile[U], old[U], last[U];
+    float acc[U];
+    int row[U];
+    bool valid[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int rr = r0 + 8 * u;
+      valid[u] = rr < rows && lt.has;
+      const int rc = rr < rows ? rr : 0;
+      const int ch = rc >= npi ? (rc >= 2 * npi ? 2 : 1) : 0;
+      const int p = rc - ch * npi;
+      row[u] = ch * GRP + p;
+      tile[u] = tiles + (uint32_t)(ch * np + p) * tile_bytes;
+      const uint32_t crow = codes + (uint32_t)(ch * np + p) * code_bytes;
       if (VIS) {
-        acc = ch == 0 ? mcol[p] : mcol[32 + p];
-        if (ch == 1) acc = (D2LO ? acc + mcol[64 + p] : acc) * d2_scale;
+        float a = ch == 0 ? mcol[p] : mcol[32 + p];
+        if (ch == 1) a = (D2LO ? a + mcol[64 + p] : a) * d2_scale;
+        acc[u] = a;
       } else {
-        acc = mcol[32 + 32 * ch + p];
+        acc[u] = mcol[32 + 32 * ch + p];
       }
-      uint32_t b = StateOps<SF>::load(tile + lt.pos);
-      if (lt.rS > 0.0f) {
-        b = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(b), omh * (acc * lt.rS)));
-        StateOps<SF>::store(tile + lt.pos, b);
+      old[u] = valid[u] ? StateOps<SF>::load(tile[u] + lt.pos) : 0u;
+      last[u] = valid[u] ? lds16(crow + lt.t2) : 0u;
+    }
+    bool changed[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      uint32_t b = old[u];
+      if (valid[u] && lt.rS > 0.0f) {
+        b = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(b), omh * (acc[u] * lt.rS)));
+        StateOps<SF>::store(tile[u] + lt.pos, b);
       }
-      if (lt.nb > 0) StateOps<SF>::store(tile + lt.b0, b);
-      if (lt.nb > 1) StateOps<SF>::store(tile + lt.b1, b);
-      if (lt.nb > 2) StateOps<SF>::store(tile + lt.b2, b);
+      if (valid[u]) {
+        if (lt.nb > 0) StateOps<SF>::store(tile[u] + lt.b0, b);
+        if (lt.nb > 1) StateOps<SF>::store(tile[u] + lt.b1, b);
+        if (lt.nb > 2) StateOps<SF>::store(tile[u] + lt.b2, b);
+      }
       uint32_t code;
       if (VIS) code = SF == 0 ? b : (uint32_t)__half_as_ushort(__float2half_rn(__uint_as_float(b)));
       else if (KIND == PV_CODE_UNORM10) code = pv::unorm10_from_float(StateOps<SF>::value(b));
       else code = SF == 0 ? pv::uf10_from_half_bits(b) : pv::uf10_from_float_bits(b);
-      changed = code != lds16(code_row + lt.t2);
+      changed[u] = valid[u] && code != last[u];
     }
-    if (__any_sync(0xffffffffu, changed) && lane == 0) flag_s[((VIS ? 3 : 0) + ch) * GRP + p] = 1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (r0 + 8 * u < rows) {                         // warp-uniform
+        if (__any_sync(0xffffffffu, changed[u]) && lane == 0) flag_s[(VIS ? 3 * GRP : 0) + row[u]] = 1;
+      }
+    }
   }
 }
 

@@ -30,47 +30,78 @@ namespace {
 constexpr int SP_THREADS = 256;
 constexpr int SP_MAX_RANGE = 512;        // probes per block (shared slot tables)
 
+// All loads of a probe's interior are issued before any is used, so a warp
+// waits for one memory round trip per probe rather than one per texel.
 __device__ __forceinline__ void pack_color_probe(const pv_dev& k, int p, int slot, int lane) {
+  constexpr int MAXQ = 3 * PV_MAX_INTERIOR * PV_MAX_INTERIOR / 32;   // 24
   const int by = slot / k.bw, bx = slot % k.bw;
   const int per = 3 * k.Tc;
-  for (int q = lane; q < per; q += 32) {
-    const int c = q / k.Tc, t = q % k.Tc, i = t / k.nc, j = t % k.nc;
-    uint16_t* dst = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(k.planes_c) +
-                                                ((size_t)c * k.ch + (size_t)by * k.nc + i) * k.cpitch) +
-                    (size_t)bx * k.nc + j;
-    if (p >= 0) {
-      const size_t at = ((size_t)c * k.P + p) * k.sc_stride + (size_t)(i + 1) * k.tc + (j + 1);
-      const uint32_t code = pv::color_code_of(k.state_c, at, k.state_fmt, k.color_code);
-      *dst = (uint16_t)(code << k.color_shift);
-      k.last_c[((size_t)c * k.P + p) * k.lc_stride + t] = (uint16_t)code;
-    } else {
-      *dst = 0;
+  uint32_t bits[MAXQ];
+#pragma unroll
+  for (int m = 0; m < MAXQ; ++m) {
+    const int q = lane + 32 * m;
+    bits[m] = 0;
+    if (q < per && p >= 0) {
+      const int c = q / k.Tc, t = q % k.Tc, i = t / k.nc, j = t % k.nc;
+      bits[m] = pv::load_state_bits(k.state_c, ((size_t)c * k.P + p) * k.sc_stride + (size_t)(i + 1) * k.tc + (j + 1),
+                                    k.state_fmt);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MAXQ; ++m) {
+    const int q = lane + 32 * m;
+    if (q < per) {
+      const int c = q / k.Tc, t = q % k.Tc, i = t / k.nc, j = t % k.nc;
+      uint16_t* dst = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(k.planes_c) +
+                                                  ((size_t)c * k.ch + (size_t)by * k.nc + i) * k.cpitch) +
+                      (size_t)bx * k.nc + j;
+      if (p >= 0) {
+        const uint32_t code = pv::color_code_of_bits(bits[m], k.state_fmt, k.color_code);
+        *dst = (uint16_t)(code << k.color_shift);
+        k.last_c[((size_t)c * k.P + p) * k.lc_stride + t] = (uint16_t)code;
+      } else {
+        *dst = 0;
+      }
     }
   }
 }
 
 __device__ __forceinline__ void pack_vis_probe(const pv_dev& k, int p, int slot, int lane) {
+  constexpr int MAXQ = PV_MAX_INTERIOR * PV_MAX_INTERIOR / 32;        // 8
   const int by = slot / k.bw, bx = slot % k.bw;
   const int n = k.nv;
-  // lanes cover (row, texel) pairs; each texel contributes four stream bytes
-  for (int q = lane; q < k.Tv; q += 32) {
-    const int i = q / n, j = q % n;
-    uint32_t c0 = 0, c1 = 0;
-    if (p >= 0) {
-      const size_t off = (size_t)(i + 1) * k.tv + (j + 1);
-      c0 = pv::vis_code_of(k.state_v, (size_t)p * k.sv_stride + off, k.state_fmt);
-      c1 = pv::vis_code_of(k.state_v, ((size_t)k.P + p) * k.sv_stride + off, k.state_fmt);
-      k.last_v[(size_t)p * k.lv_stride + q] = (uint16_t)c0;
-      k.last_v[((size_t)k.P + p) * k.lv_stride + q] = (uint16_t)c1;
-    }
-    const uint32_t bytes[4] = {c0 & 0xFFu, c0 >> 8, c1 & 0xFFu, c1 >> 8};
-    const size_t y = (size_t)by * n + i;
-    const int s0 = 4 * (bx * n + j);
+  uint32_t b0[MAXQ], b1[MAXQ];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int sb = s0 + b;
-      const int pl = sb % 3;
-      k.planes_v[((size_t)pl * k.vh + y) * k.vpitch + (size_t)(sb / 3)] = (uint8_t)bytes[b];
+  for (int m = 0; m < MAXQ; ++m) {
+    const int q = lane + 32 * m;
+    b0[m] = b1[m] = 0;
+    if (q < k.Tv && p >= 0) {
+      const size_t off = (size_t)(q / n + 1) * k.tv + (q % n + 1);
+      b0[m] = pv::load_state_bits(k.state_v, (size_t)p * k.sv_stride + off, k.state_fmt);
+      b1[m] = pv::load_state_bits(k.state_v, ((size_t)k.P + p) * k.sv_stride + off, k.state_fmt);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MAXQ; ++m) {
+    const int q = lane + 32 * m;
+    if (q < k.Tv) {
+      const int i = q / n, j = q % n;
+      uint32_t c0 = 0, c1 = 0;
+      if (p >= 0) {
+        c0 = pv::vis_code_of_bits(b0[m], k.state_fmt);
+        c1 = pv::vis_code_of_bits(b1[m], k.state_fmt);
+        k.last_v[(size_t)p * k.lv_stride + q] = (uint16_t)c0;
+        k.last_v[((size_t)k.P + p) * k.lv_stride + q] = (uint16_t)c1;
+      }
+      const uint32_t bytes[4] = {c0 & 0xFFu, c0 >> 8, c1 & 0xFFu, c1 >> 8};
+      const size_t y = (size_t)by * n + i;
+      const int s0 = 4 * (bx * n + j);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int sb = s0 + b;
+        const int pl = sb % 3;
+        k.planes_v[((size_t)pl * k.vh + y) * k.vpitch + (size_t)(sb / 3)] = (uint8_t)bytes[b];
+      }
     }
   }
 }
@@ -93,11 +124,22 @@ __global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range)
   const int b = min(k.P, tid * per), e = min(k.P, b + per);
   int nc = 0, nv = 0, lastc = -1, lastv = -1;
   if (fresh) {
-    for (int p = b; p < e; ++p) {
-      const int fc = k.flags[p] | k.flags[(size_t)k.P + p] | k.flags[2 * (size_t)k.P + p];
-      const int fv = k.flags[3 * (size_t)k.P + p] | k.flags[4 * (size_t)k.P + p];
-      if (fc) { ++nc; lastc = p; }
-      if (fv) { ++nv; lastv = p; }
+    for (int p0 = b; p0 < e; p0 += 8) {               // loads of 8 probes in flight at once
+      uint32_t fc[8], fv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int p = p0 + u;
+        fc[u] = fv[u] = 0;
+        if (p < e) {
+          fc[u] = k.flags[p] | k.flags[(size_t)k.P + p] | k.flags[2 * (size_t)k.P + p];
+          fv[u] = k.flags[3 * (size_t)k.P + p] | k.flags[4 * (size_t)k.P + p];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (fc[u]) { ++nc; lastc = p0 + u; }
+        if (fv[u]) { ++nv; lastv = p0 + u; }
+      }
     }
   }
   int ic = nc, iv = nv, mc = lastc, mv = lastv;        // inclusive sums / running max
@@ -186,8 +228,8 @@ cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int range = (k.P + sms - 1) / sms;
-  if (range < 8) range = 8;
+  int range = (k.P + 4 * sms - 1) / (4 * sms);       // about four blocks per SM
+  if (range < 4) range = 4;
   if (range > SP_MAX_RANGE) range = SP_MAX_RANGE;
   const int blocks = (k.P + range - 1) / range;
   k_select_pack<<<blocks, SP_THREADS, 0, st>>>(k, range);
