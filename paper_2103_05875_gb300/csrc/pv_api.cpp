@@ -117,7 +117,7 @@ Layout layout_of(const pv_desc* d) {
   L.off_state_v = take((size_t)2 * L.P * L.sv_stride * L.sb);
   L.off_last_c = take((size_t)3 * L.P * L.lc_stride * 2);
   L.off_last_v = take((size_t)2 * L.P * L.lv_stride * 2);
-  L.off_flags = take((size_t)5 * L.P);
+  L.off_flags = take((size_t)2 * ((L.P + 31) / 32) * 4);
   L.off_wrt = take((size_t)L.R * (L.Tc + L.Tv) * 4);
   L.off_sums = take((size_t)(L.Tc + L.Tv) * 4);
   // operand weights: F16 one binary16 plane, BF16 hi + lo bfloat16 planes, F32 hi + lo float planes
@@ -229,7 +229,8 @@ pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
   k.state_v = b + L.off_state_v;
   k.last_c = (uint16_t*)(b + L.off_last_c);
   k.last_v = (uint16_t*)(b + L.off_last_v);
-  k.flags = (uint8_t*)(b + L.off_flags);
+  k.chg = (uint32_t*)(b + L.off_flags);
+  k.chg_words = (L.P + 31) / 32;
   k.w_rt = (float*)(b + L.off_wrt);
   k.sums = (float*)(b + L.off_sums);
   k.w_op = b + L.off_wop;
@@ -473,6 +474,7 @@ pv_status probe_volume_import_state(pv_volume* v, const void* tiles_c, const voi
   static const unsigned long long never = ~0ull;      // imported flags count as fresh
   if (e == cudaSuccess) e = cudaMemcpyAsync(k.frame, &f, sizeof f, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(k.sel_frame, &never, sizeof never, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(k.chg, 0, (size_t)2 * k.chg_words * 4, st);
   if (e == cudaSuccess) e = pv_launch_recompute_flags(k, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "import");

@@ -173,9 +173,14 @@ __global__ void __launch_bounds__(NT) k_blend_simt(pv_dev k, const Tin* __restri
     }
   }
   __syncthreads();
-  for (int q = tid; q < 5 * G; q += NT) {
-    const int g = q % G, ch5 = q / G;
-    if (p0 + g < k.P) k.flags[(size_t)ch5 * k.P + p0 + g] = (uint8_t)flag_s[q];
+  if (tid < 2) {                      // changed-probe bits of this block's probes
+    uint32_t mask = 0;
+    for (int g = 0; g < G && p0 + g < k.P; ++g) {
+      const int f = tid == 0 ? (flag_s[0 * G + g] | flag_s[1 * G + g] | flag_s[2 * G + g])
+                             : (flag_s[3 * G + g] | flag_s[4 * G + g]);
+      if (f) mask |= 1u << ((p0 + g) & 31);
+    }
+    if (mask) atomicOr(&k.chg[tid * k.chg_words + (p0 >> 5)], mask);
   }
 }
 

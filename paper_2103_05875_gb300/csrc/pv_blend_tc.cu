@@ -45,6 +45,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdio.h>
+#include <type_traits>
 #include <string.h>
 
 #include "pv_codes.cuh"
@@ -213,31 +214,12 @@ __device__ __forceinline__ uint64_t pack_border(int i, int j, int n) {
   return v | ((uint64_t)m << 48);
 }
 
-__device__ __forceinline__ uint32_t lds16(uint32_t a) {
-  uint16_t v;
-  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ uint32_t lds32(uint32_t a) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ void sts16(uint32_t a, uint32_t v) {
-  asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v) : "memory");
-}
-__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
-  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-
-// State format as a compile-time choice: 0 binary16, 1 binary32.
+// State format as a compile-time choice: 0 binary16, 1 binary32. Tiles are
+// addressed in elements through typed shared-memory pointers so the compiler
+// can schedule the epilogue's loads and stores freely.
 template <int SF>
 struct StateOps {
-  static __device__ __forceinline__ uint32_t load(uint32_t a) { return SF == 0 ? lds16(a) : lds32(a); }
-  static __device__ __forceinline__ void store(uint32_t a, uint32_t b) {
-    if (SF == 0) sts16(a, b);
-    else sts32(a, b);
-  }
+  using T = typename std::conditional<SF == 0, uint16_t, uint32_t>::type;
   static __device__ __forceinline__ float value(uint32_t b) {
     return SF == 0 ? __half2float(__ushort_as_half((unsigned short)b)) : __uint_as_float(b);
   }
@@ -248,11 +230,11 @@ struct StateOps {
 
 // Per-lane constants of the texel a lane handles in an epilogue pass.
 struct LaneTexel {
-  bool has;
-  uint32_t pos, b0, b1, b2;   // byte offsets in the tile: texel and its guard-band copies
-  int nb;
+  uint32_t pos, b0, b1, b2;   // element offsets in the tile: the texel and its guard-band copies
+  int nb;                     // number of guard-band copies (0 for lanes without a texel)
   float rS;                   // 1 / weight sum (0: no weight, the texel keeps its value)
-  uint32_t t2;                // byte offset of the texel's code in a code row
+  int t;                      // texel index (code offset in a code row)
+  bool has;
 };
 
 // One pass of the fused epilogue: every probe row (ch, p) of this texture, one
@@ -261,53 +243,47 @@ struct LaneTexel {
 // row's changed flag is raised when any transmitted code differs from the
 // last-transmitted one.
 template <int SF, int KIND, bool VIS, bool D2LO>
-__device__ __forceinline__ void epi_rows(const LaneTexel& lt, const float* mcol, int rows, int npi, int np,
-                                         uint32_t tiles, uint32_t tile_bytes, uint32_t codes, uint32_t code_bytes,
-                                         float h, float omh, float d2_scale, int ew, int lane, int* flag_s) {
+__device__ __forceinline__ void epi_rows(const LaneTexel lt, const float* __restrict__ mcol, int rows, int npi,
+                                         int np, void* tiles_v, int tile_elems, const uint16_t* __restrict__ codes,
+                                         int code_elems, float h, float omh, float d2_scale, int ew, int lane,
+                                         int* flag_s) {
+  using ST = typename StateOps<SF>::T;
+  ST* tiles = reinterpret_cast<ST*>(tiles_v);
   constexpr int U = 4;                                 // independent rows per warp iteration
   for (int r0 = ew; r0 < rows; r0 += 8 * U) {
-    uint32_t tile[U], old[U], last[U];
-    float acc[U];
+    bool changed[U];
     int row[U];
-    bool valid[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int rr = r0 + 8 * u;
-      valid[u] = rr < rows && lt.has;
-      const int rc = rr < rows ? rr : 0;
+      const bool live = rr < rows;
+      const int rc = live ? rr : 0;
       const int ch = rc >= npi ? (rc >= 2 * npi ? 2 : 1) : 0;
       const int p = rc - ch * npi;
       row[u] = ch * GRP + p;
-      tile[u] = tiles + (uint32_t)(ch * np + p) * tile_bytes;
-      const uint32_t crow = codes + (uint32_t)(ch * np + p) * code_bytes;
+      ST* tile = tiles + (ch * np + p) * tile_elems;
+      float acc;
       if (VIS) {
-        float a = ch == 0 ? mcol[p] : mcol[32 + p];
-        if (ch == 1) a = (D2LO ? a + mcol[64 + p] : a) * d2_scale;
-        acc[u] = a;
+        acc = ch == 0 ? mcol[p] : mcol[32 + p];
+        if (ch == 1) acc = (D2LO ? acc + mcol[64 + p] : acc) * d2_scale;
       } else {
-        acc[u] = mcol[32 + 32 * ch + p];
+        acc = mcol[32 + 32 * ch + p];
       }
-      old[u] = valid[u] ? StateOps<SF>::load(tile[u] + lt.pos) : 0u;
-      last[u] = valid[u] ? lds16(crow + lt.t2) : 0u;
-    }
-    bool changed[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      uint32_t b = old[u];
-      if (valid[u] && lt.rS > 0.0f) {
-        b = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(b), omh * (acc[u] * lt.rS)));
-        StateOps<SF>::store(tile[u] + lt.pos, b);
-      }
-      if (valid[u]) {
-        if (lt.nb > 0) StateOps<SF>::store(tile[u] + lt.b0, b);
-        if (lt.nb > 1) StateOps<SF>::store(tile[u] + lt.b1, b);
-        if (lt.nb > 2) StateOps<SF>::store(tile[u] + lt.b2, b);
-      }
+      const bool v = live && lt.has;
+      uint32_t b = v ? (uint32_t)tile[lt.pos] : 0u;
+      const uint32_t last = v ? (uint32_t)codes[(ch * np + p) * code_elems + lt.t] : 0u;
+      const uint32_t nbits = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(b), omh * (acc * lt.rS)));
+      const bool upd = v && lt.rS > 0.0f;
+      b = upd ? nbits : b;
+      if (upd) tile[lt.pos] = (ST)b;
+      if (v && lt.nb > 0) tile[lt.b0] = (ST)b;
+      if (v && lt.nb > 1) tile[lt.b1] = (ST)b;
+      if (v && lt.nb > 2) tile[lt.b2] = (ST)b;
       uint32_t code;
       if (VIS) code = SF == 0 ? b : (uint32_t)__half_as_ushort(__float2half_rn(__uint_as_float(b)));
       else if (KIND == PV_CODE_UNORM10) code = pv::unorm10_from_float(StateOps<SF>::value(b));
       else code = SF == 0 ? pv::uf10_from_half_bits(b) : pv::uf10_from_float_bits(b);
-      changed[u] = valid[u] && code != last[u];
+      changed[u] = v && code != last;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -612,29 +588,29 @@ __global__ void __launch_bounds__(NT, 1)
         lt.has = t < T;
         const int tg = lt.has ? (vis ? k.Tc + t : t) : 0;
         const uint64_t bord = tab_border[tg];
-        lt.pos = (uint32_t)tab_pos[tg] * sb;
-        lt.nb = (int)(bord >> 48);
-        lt.b0 = (uint32_t)(bord & 0xFFFFu) * sb;
-        lt.b1 = (uint32_t)((bord >> 16) & 0xFFFFu) * sb;
-        lt.b2 = (uint32_t)((bord >> 32) & 0xFFFFu) * sb;
+        lt.pos = tab_pos[tg];
+        lt.nb = lt.has ? (int)(bord >> 48) : 0;
+        lt.b0 = (uint32_t)(bord & 0xFFFFu);
+        lt.b1 = (uint32_t)((bord >> 16) & 0xFFFFu);
+        lt.b2 = (uint32_t)((bord >> 32) & 0xFFFFu);
         lt.rS = lt.has ? rsum[(vis ? tp.Nc : 0) + t] : 0.0f;
-        lt.t2 = (uint32_t)t * 2;
+        lt.t = lt.has ? t : 0;
         const float* mcol = ms + lane * MS_LD;
         const int rows = (vis ? 2 : 3) * npi;
-        const uint32_t tiles = smem_u32(vis ? st_v : st_c);
-        const uint32_t tile_bytes = (uint32_t)(vis ? k.sv_stride : k.sc_stride) * sb;
-        const uint32_t codes = smem_u32(vis ? ls_v : ls_c);
-        const uint32_t code_bytes = (uint32_t)(vis ? k.lv_stride : k.lc_stride) * 2;
+        void* tiles = vis ? (void*)st_v : (void*)st_c;
+        const int tile_elems = vis ? k.sv_stride : k.sc_stride;
+        const uint16_t* codes = vis ? ls_v : ls_c;
+        const int code_elems = vis ? k.lv_stride : k.lc_stride;
         const bool f16 = k.state_fmt == PV_FMT_F16;
         if (vis) {
-          if (f16) epi_rows<0, 0, true, d2_lo>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, d2_scale, ew, lane, flag_s);
-          else epi_rows<1, 0, true, d2_lo>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, d2_scale, ew, lane, flag_s);
+          if (f16) epi_rows<0, 0, true, d2_lo>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, d2_scale, ew, lane, flag_s);
+          else epi_rows<1, 0, true, d2_lo>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, d2_scale, ew, lane, flag_s);
         } else if (kind == PV_CODE_UNORM10) {
-          if (f16) epi_rows<0, PV_CODE_UNORM10, false, false>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, 1.0f, ew, lane, flag_s);
-          else epi_rows<1, PV_CODE_UNORM10, false, false>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, 1.0f, ew, lane, flag_s);
+          if (f16) epi_rows<0, PV_CODE_UNORM10, false, false>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_s);
+          else epi_rows<1, PV_CODE_UNORM10, false, false>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_s);
         } else {
-          if (f16) epi_rows<0, PV_CODE_UF10, false, false>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, 1.0f, ew, lane, flag_s);
-          else epi_rows<1, PV_CODE_UF10, false, false>(lt, mcol, rows, npi, np, tiles, tile_bytes, codes, code_bytes, h, omh, 1.0f, ew, lane, flag_s);
+          if (f16) epi_rows<0, PV_CODE_UF10, false, false>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_s);
+          else epi_rows<1, PV_CODE_UF10, false, false>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_s);
         }
         epi_bar();
       }
@@ -645,11 +621,21 @@ __global__ void __launch_bounds__(NT, 1)
         b = 0;
         tph ^= 1;
       }
-      for (int q = e; q < 5 * npi; q += EPI_THREADS) {
-        const int ch5 = q / npi, p = q % npi;
-        k.flags[(size_t)ch5 * k.P + p0 + p] = (uint8_t)flag_s[ch5 * GRP + p];
-        flag_s[ch5 * GRP + p] = 0;
+      if (e < 2) {                                     // changed-probe bits of this item
+        const int w0 = p0 >> 5, w1 = (p0 + npi - 1) >> 5;
+        for (int w = w0; w <= w1; ++w) {
+          uint32_t mask = 0;
+          for (int p = 0; p < npi; ++p) {
+            if (((p0 + p) >> 5) != w) continue;
+            const int f = e == 0 ? (flag_s[p] | flag_s[GRP + p] | flag_s[2 * GRP + p])
+                                 : (flag_s[3 * GRP + p] | flag_s[4 * GRP + p]);
+            if (f) mask |= 1u << ((p0 + p) & 31);
+          }
+          if (mask) atomicOr(&k.chg[e * k.chg_words + w], mask);
+        }
       }
+      epi_bar();
+      for (int q = e; q < 5 * GRP; q += EPI_THREADS) flag_s[q] = 0;
       fence_proxy_async();
       epi_bar();
       if (e == 0) {

@@ -23,7 +23,9 @@ struct pv_dev {
   void* state_v;                        // [2][P][sv_stride]
   uint16_t* last_c;                     // [3][P][lc_stride], first Tc codes used
   uint16_t* last_v;                     // [2][P][lv_stride]
-  uint8_t* flags;                       // [5][P]: colour R,G,B then d, d^2 changed
+  uint32_t* chg;                        // [2][chg_words]: changed-probe bits, colour then
+                                        // visibility, bit p%32 of word p/32
+  int chg_words;                        // words per texture: ceil(P / 32)
   float* w_rt;                          // [R][Tc + Tv] weights, ray-major (SIMT blend)
   float* sums;                          // [Tc + Tv] weight sums
   void* w_op;                           // [planes][tc_pad + tv_pad][r_pad] weights, texel-major, operand

@@ -2,12 +2,13 @@
 // 3.4 of arXiv 2103.05875), fused into one kernel, plus the flag
 // recomputation used after a state import.
 //
-// Selection: a probe is sent iff any of its channel flags (raised by the
-// blend when a transmitted code differs from the last-transmitted one) is
-// set; slots are assigned in ascending probe id. Every block scans all flags
-// (a few bytes per probe, from L2), so each block knows the slot of every
-// probe and the total without a grid-wide synchronisation; it then packs its
-// own contiguous range of probes, one warp per probe:
+// Selection: the blend raises bit p of the colour (visibility) mask when a
+// transmitted code of probe p differs from its last-transmitted code; slots
+// are assigned in ascending probe id. Each block reads both masks (P/8 bytes
+// each) and reduces them, so it knows its probes' slots, the last selected
+// probe before its range (for the delta code) and the totals without any
+// grid-wide synchronisation. It then packs its own contiguous probe range, one
+// warp per probe:
 //   colour: the 10-bit codes of the interior go to planes Y=R, U=G, V=B at
 //           block (k / B_w, k % B_w) as 16-bit samples (code << 6 unless
 //           color_lsb), and to the last-transmitted texture;
@@ -16,49 +17,54 @@
 //           column s div 3 (the paper's YUVY / UVYU / VYUV pattern). Byte
 //           stores, because neighbouring slots share plane words.
 // Each block writes its probes' index-buffer entries and deltas
-// (d0 = id0, dk = id_k - id_(k-1)); slots that held a probe last frame but
-// are empty now are cleared (slots beyond both counts are already zero).
-// Flags count only once per update: the kernel compares the frame counter
-// with the frame of the previous select, so a second select without a new
-// update selects nothing. The last block to finish advances the select
-// sequence (which double-buffers the previous counts).
+// (d0 = id0, dk = id_k - id_(k-1)), and clears its share of the slots that
+// held a probe last frame but are empty now (slots beyond both counts are
+// already zero). The masks count once per update: the kernel compares the
+// frame counter with the frame of the previous select, so a second select
+// without a new update selects nothing. The last block to finish advances the
+// select sequence, which double-buffers the previous counts.
 #include "pv_codes.cuh"
 #include "pv_internal.h"
 
 namespace {
 
 constexpr int SP_THREADS = 256;
-constexpr int SP_MAX_RANGE = 512;        // probes per block (shared slot tables)
+constexpr int SP_WARPS = SP_THREADS / 32;
+constexpr int SP_MAX_RANGE = 512;        // probes per block
+constexpr int SP_MAX_TEX = 3 * PV_MAX_INTERIOR * PV_MAX_INTERIOR;
 
-// All loads of a probe's interior are issued before any is used, so a warp
-// waits for one memory round trip per probe rather than one per texel.
-__device__ __forceinline__ void pack_color_probe(const pv_dev& k, int p, int slot, int lane) {
-  constexpr int MAXQ = 3 * PV_MAX_INTERIOR * PV_MAX_INTERIOR / 32;   // 24
+struct SpTables {
+  uint32_t col[SP_MAX_TEX];   // colour (c, t): c << 24 | tile_pos << 12 | i << 6 | j
+  uint32_t vis[PV_MAX_INTERIOR * PV_MAX_INTERIOR];   // visibility t: tile_pos << 12 | i << 6 | j
+};
+
+// Colour block of slot `slot` from probe p (p < 0: clear the block). Loads of
+// four codes per lane are issued before any of them is used.
+__device__ __forceinline__ void pack_color_probe(const pv_dev& k, const SpTables& tb, int p, int slot, int lane) {
   const int by = slot / k.bw, bx = slot % k.bw;
   const int per = 3 * k.Tc;
-  uint32_t bits[MAXQ];
+  uint8_t* plane0 = reinterpret_cast<uint8_t*>(k.planes_c) + (size_t)by * k.nc * k.cpitch + (size_t)bx * k.nc * 2;
+  for (int q0 = 0; q0 < per; q0 += 128) {
+    uint32_t bits[4], ent[4];
 #pragma unroll
-  for (int m = 0; m < MAXQ; ++m) {
-    const int q = lane + 32 * m;
-    bits[m] = 0;
-    if (q < per && p >= 0) {
-      const int c = q / k.Tc, t = q % k.Tc, i = t / k.nc, j = t % k.nc;
-      bits[m] = pv::load_state_bits(k.state_c, ((size_t)c * k.P + p) * k.sc_stride + (size_t)(i + 1) * k.tc + (j + 1),
-                                    k.state_fmt);
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + lane + 32 * u;
+      ent[u] = q < per ? tb.col[q] : 0xFFFFFFFFu;
+      bits[u] = 0;
+      if (q < per && p >= 0) {
+        const uint32_t c = ent[u] >> 24, pos = (ent[u] >> 12) & 0xFFFu;
+        bits[u] = pv::load_state_bits(k.state_c, ((size_t)c * k.P + p) * k.sc_stride + pos, k.state_fmt);
+      }
     }
-  }
 #pragma unroll
-  for (int m = 0; m < MAXQ; ++m) {
-    const int q = lane + 32 * m;
-    if (q < per) {
-      const int c = q / k.Tc, t = q % k.Tc, i = t / k.nc, j = t % k.nc;
-      uint16_t* dst = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(k.planes_c) +
-                                                  ((size_t)c * k.ch + (size_t)by * k.nc + i) * k.cpitch) +
-                      (size_t)bx * k.nc + j;
+    for (int u = 0; u < 4; ++u) {
+      if (ent[u] == 0xFFFFFFFFu) continue;
+      const uint32_t c = ent[u] >> 24, i = (ent[u] >> 6) & 63u, j = ent[u] & 63u;
+      uint16_t* dst = reinterpret_cast<uint16_t*>(plane0 + ((size_t)c * k.ch + i) * k.cpitch) + j;
       if (p >= 0) {
-        const uint32_t code = pv::color_code_of_bits(bits[m], k.state_fmt, k.color_code);
+        const uint32_t code = pv::color_code_of_bits(bits[u], k.state_fmt, k.color_code);
         *dst = (uint16_t)(code << k.color_shift);
-        k.last_c[((size_t)c * k.P + p) * k.lc_stride + t] = (uint16_t)code;
+        k.last_c[((size_t)c * k.P + p) * k.lc_stride + i * k.nc + j] = (uint16_t)code;
       } else {
         *dst = 0;
       }
@@ -66,32 +72,33 @@ __device__ __forceinline__ void pack_color_probe(const pv_dev& k, int p, int slo
   }
 }
 
-__device__ __forceinline__ void pack_vis_probe(const pv_dev& k, int p, int slot, int lane) {
-  constexpr int MAXQ = PV_MAX_INTERIOR * PV_MAX_INTERIOR / 32;        // 8
+// Visibility block of slot `slot` from probe p (p < 0: clear the block).
+__device__ __forceinline__ void pack_vis_probe(const pv_dev& k, const SpTables& tb, int p, int slot, int lane) {
   const int by = slot / k.bw, bx = slot % k.bw;
   const int n = k.nv;
-  uint32_t b0[MAXQ], b1[MAXQ];
+  for (int q0 = 0; q0 < k.Tv; q0 += 128) {
+    uint32_t b0[4], b1[4], ent[4];
 #pragma unroll
-  for (int m = 0; m < MAXQ; ++m) {
-    const int q = lane + 32 * m;
-    b0[m] = b1[m] = 0;
-    if (q < k.Tv && p >= 0) {
-      const size_t off = (size_t)(q / n + 1) * k.tv + (q % n + 1);
-      b0[m] = pv::load_state_bits(k.state_v, (size_t)p * k.sv_stride + off, k.state_fmt);
-      b1[m] = pv::load_state_bits(k.state_v, ((size_t)k.P + p) * k.sv_stride + off, k.state_fmt);
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + lane + 32 * u;
+      ent[u] = q < k.Tv ? tb.vis[q] : 0xFFFFFFFFu;
+      b0[u] = b1[u] = 0;
+      if (q < k.Tv && p >= 0) {
+        const uint32_t pos = ent[u] >> 12;
+        b0[u] = pv::load_state_bits(k.state_v, (size_t)p * k.sv_stride + pos, k.state_fmt);
+        b1[u] = pv::load_state_bits(k.state_v, ((size_t)k.P + p) * k.sv_stride + pos, k.state_fmt);
+      }
     }
-  }
 #pragma unroll
-  for (int m = 0; m < MAXQ; ++m) {
-    const int q = lane + 32 * m;
-    if (q < k.Tv) {
-      const int i = q / n, j = q % n;
+    for (int u = 0; u < 4; ++u) {
+      if (ent[u] == 0xFFFFFFFFu) continue;
+      const int i = (int)((ent[u] >> 6) & 63u), j = (int)(ent[u] & 63u);
       uint32_t c0 = 0, c1 = 0;
       if (p >= 0) {
-        c0 = pv::vis_code_of_bits(b0[m], k.state_fmt);
-        c1 = pv::vis_code_of_bits(b1[m], k.state_fmt);
-        k.last_v[(size_t)p * k.lv_stride + q] = (uint16_t)c0;
-        k.last_v[((size_t)k.P + p) * k.lv_stride + q] = (uint16_t)c1;
+        c0 = pv::vis_code_of_bits(b0[u], k.state_fmt);
+        c1 = pv::vis_code_of_bits(b1[u], k.state_fmt);
+        k.last_v[(size_t)p * k.lv_stride + i * n + j] = (uint16_t)c0;
+        k.last_v[((size_t)k.P + p) * k.lv_stride + i * n + j] = (uint16_t)c1;
       }
       const uint32_t bytes[4] = {c0 & 0xFFu, c0 >> 8, c1 & 0xFFu, c1 >> 8};
       const size_t y = (size_t)by * n + i;
@@ -106,108 +113,112 @@ __device__ __forceinline__ void pack_vis_probe(const pv_dev& k, int p, int slot,
   }
 }
 
+// Block-wide sums (and maxima) of three values over all threads.
+__device__ __forceinline__ void block_reduce3(int& a, int& b, int& c, int* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
+  }
+  if (lane == 0) { sh[3 * wid] = a; sh[3 * wid + 1] = b; sh[3 * wid + 2] = c; }
+  __syncthreads();
+  a = 0; b = 0; c = -1;
+  for (int w = 0; w < SP_WARPS; ++w) { a += sh[3 * w]; b += sh[3 * w + 1]; c = max(c, sh[3 * w + 2]); }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range) {
-  __shared__ int warp_c[SP_THREADS / 32], warp_v[SP_THREADS / 32];
-  __shared__ int warp_lc[SP_THREADS / 32], warp_lv[SP_THREADS / 32];
+  __shared__ SpTables tb;
+  __shared__ int red[3 * SP_WARPS];
   __shared__ int slot_c[SP_MAX_RANGE], slot_v[SP_MAX_RANGE];
   __shared__ uint16_t prev_c[SP_MAX_RANGE], prev_v[SP_MAX_RANGE];
-  __shared__ int tot_c, tot_v;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const bool fresh = *k.frame != *k.sel_frame;
   const uint32_t seq = k.sel[0];
   const uint32_t par = seq & 1u;
   const int prev_cnt_c = (int)k.sel[2 + 2 * (par ^ 1u)], prev_cnt_v = (int)k.sel[3 + 2 * (par ^ 1u)];
   const int pb = blockIdx.x * range, pe = min(k.P, pb + range);
+  const int W = k.chg_words, wb = pb >> 5;
 
-  // 1. scan of every probe's flags
-  const int per = (k.P + SP_THREADS - 1) / SP_THREADS;
-  const int b = min(k.P, tid * per), e = min(k.P, b + per);
-  int nc = 0, nv = 0, lastc = -1, lastv = -1;
+  for (int q = tid; q < 3 * k.Tc; q += SP_THREADS) {
+    const int c = q / k.Tc, t = q % k.Tc, i = t / k.nc, j = t % k.nc;
+    tb.col[q] = ((uint32_t)c << 24) | ((uint32_t)((i + 1) * k.tc + j + 1) << 12) | ((uint32_t)i << 6) | (uint32_t)j;
+  }
+  for (int t = tid; t < k.Tv; t += SP_THREADS) {
+    const int i = t / k.nv, j = t % k.nv;
+    tb.vis[t] = ((uint32_t)((i + 1) * k.tv + j + 1) << 12) | ((uint32_t)i << 6) | (uint32_t)j;
+  }
+
+  // 1. totals, selected probes before this block's first word, last of them
+  int tot_c = 0, tot_v = 0, dummy = -1;
+  int bef_c = 0, bef_v = 0, last_c = -1, last_v = -1;
   if (fresh) {
-    for (int p0 = b; p0 < e; p0 += 8) {               // loads of 8 probes in flight at once
-      uint32_t fc[8], fv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int p = p0 + u;
-        fc[u] = fv[u] = 0;
-        if (p < e) {
-          fc[u] = k.flags[p] | k.flags[(size_t)k.P + p] | k.flags[2 * (size_t)k.P + p];
-          fv[u] = k.flags[3 * (size_t)k.P + p] | k.flags[4 * (size_t)k.P + p];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (fc[u]) { ++nc; lastc = p0 + u; }
-        if (fv[u]) { ++nv; lastv = p0 + u; }
+    for (int w = tid; w < W; w += SP_THREADS) {
+      const uint32_t mc = k.chg[w], mv = k.chg[W + w];
+      tot_c += __popc(mc);
+      tot_v += __popc(mv);
+      if (w < wb) {
+        bef_c += __popc(mc);
+        bef_v += __popc(mv);
+        if (mc) last_c = max(last_c, 32 * w + 31 - __clz(mc));
+        if (mv) last_v = max(last_v, 32 * w + 31 - __clz(mv));
       }
     }
   }
-  int ic = nc, iv = nv, mc = lastc, mv = lastv;        // inclusive sums / running max
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int yc = __shfl_up_sync(0xffffffffu, ic, o), yv = __shfl_up_sync(0xffffffffu, iv, o);
-    const int zc = __shfl_up_sync(0xffffffffu, mc, o), zv = __shfl_up_sync(0xffffffffu, mv, o);
-    if (lane >= o) { ic += yc; iv += yv; mc = max(mc, zc); mv = max(mv, zv); }
-  }
-  if (lane == 31) { warp_c[wid] = ic; warp_v[wid] = iv; warp_lc[wid] = mc; warp_lv[wid] = mv; }
-  __syncthreads();
+  block_reduce3(tot_c, tot_v, dummy, red);
+  int zero_c = 0;
+  block_reduce3(bef_c, zero_c, last_c, red);
+  int zero_v = 0;
+  block_reduce3(bef_v, zero_v, last_v, red);
+
+  // 2. slots of this block's probes: walk its words in order (thread 0; at
+  //    most a few words per block)
   if (tid == 0) {
-    int sc = 0, sv = 0, lc = -1, lv = -1;
-    for (int w = 0; w < SP_THREADS / 32; ++w) {
-      const int a = warp_c[w], bb = warp_v[w], x = warp_lc[w], y = warp_lv[w];
-      warp_c[w] = sc; warp_v[w] = sv; warp_lc[w] = lc; warp_lv[w] = lv;
-      sc += a; sv += bb; lc = max(lc, x); lv = max(lv, y);
-    }
-    tot_c = sc; tot_v = sv;
-  }
-  __syncthreads();
-  // exclusive prefix and last selected probe before this thread's chunk
-  int rc = warp_c[wid] + ic - nc, rv = warp_v[wid] + iv - nv;
-  const int up_c = __shfl_up_sync(0xffffffffu, mc, 1), up_v = __shfl_up_sync(0xffffffffu, mv, 1);
-  int lc = max(warp_lc[wid], lane > 0 ? up_c : -1);
-  int lv = max(warp_lv[wid], lane > 0 ? up_v : -1);
-  // 2. slots of this block's probes
-  if (fresh) {
-    for (int p = b; p < e; ++p) {
-      const int fc = k.flags[p] | k.flags[(size_t)k.P + p] | k.flags[2 * (size_t)k.P + p];
-      const int fv = k.flags[3 * (size_t)k.P + p] | k.flags[4 * (size_t)k.P + p];
-      if (p >= pb && p < pe) {
-        slot_c[p - pb] = fc ? rc : -1;
-        slot_v[p - pb] = fv ? rv : -1;
-        prev_c[p - pb] = (uint16_t)(lc < 0 ? 0 : lc);
-        prev_v[p - pb] = (uint16_t)(lv < 0 ? 0 : lv);
+    int rc = bef_c, rv = bef_v, lc = last_c, lv = last_v;
+    for (int w = wb; w <= ((pe - 1) >> 5) && pb < pe; ++w) {
+      const uint32_t mc = fresh ? k.chg[w] : 0u, mv = fresh ? k.chg[W + w] : 0u;
+      for (int bit = 0; bit < 32; ++bit) {
+        const int p = 32 * w + bit;
+        if (p >= pe) break;
+        const bool sc = (mc >> bit) & 1u, sv = (mv >> bit) & 1u;
+        if (p >= pb) {
+          slot_c[p - pb] = sc ? rc : -1;
+          slot_v[p - pb] = sv ? rv : -1;
+          prev_c[p - pb] = (uint16_t)(lc < 0 ? 0 : lc);
+          prev_v[p - pb] = (uint16_t)(lv < 0 ? 0 : lv);
+        }
+        if (sc) { ++rc; lc = p; }
+        if (sv) { ++rv; lv = p; }
       }
-      if (fc) { ++rc; lc = p; }
-      if (fv) { ++rv; lv = p; }
     }
-  } else {
-    for (int p = max(b, pb); p < min(e, pe); ++p) { slot_c[p - pb] = -1; slot_v[p - pb] = -1; }
   }
   __syncthreads();
-  const int cnt_c = tot_c, cnt_v = tot_v;
+
   // 3. pack this block's selected probes, one warp per probe
-  for (int p = pb + wid; p < pe; p += SP_THREADS / 32) {
+  for (int p = pb + wid; p < pe; p += SP_WARPS) {
     const int sc = slot_c[p - pb], sv = slot_v[p - pb];
     if (sc >= 0) {
-      pack_color_probe(k, p, sc, lane);
+      pack_color_probe(k, tb, p, sc, lane);
       if (lane == 0) { k.idx_c[sc] = (uint16_t)p; k.delta_c[sc] = (uint16_t)(p - prev_c[p - pb]); }
     }
     if (sv >= 0) {
-      pack_vis_probe(k, p, sv, lane);
+      pack_vis_probe(k, tb, p, sv, lane);
       if (lane == 0) { k.idx_v[sv] = (uint16_t)p; k.delta_v[sv] = (uint16_t)(p - prev_v[p - pb]); }
     }
   }
   // 4. clear slots used by the previous frame and empty now
-  for (int s = cnt_c + blockIdx.x * (SP_THREADS / 32) + wid; s < prev_cnt_c; s += gridDim.x * (SP_THREADS / 32))
-    pack_color_probe(k, -1, s, lane);
-  for (int s = cnt_v + blockIdx.x * (SP_THREADS / 32) + wid; s < prev_cnt_v; s += gridDim.x * (SP_THREADS / 32))
-    pack_vis_probe(k, -1, s, lane);
+  for (int s = tot_c + blockIdx.x * SP_WARPS + wid; s < prev_cnt_c; s += gridDim.x * SP_WARPS)
+    pack_color_probe(k, tb, -1, s, lane);
+  for (int s = tot_v + blockIdx.x * SP_WARPS + wid; s < prev_cnt_v; s += gridDim.x * SP_WARPS)
+    pack_vis_probe(k, tb, -1, s, lane);
   // 5. counts, and the select sequence once every block is done
   if (blockIdx.x == 0 && tid == 0) {
-    k.counts[0] = (uint32_t)cnt_c;
-    k.counts[1] = (uint32_t)cnt_v;
-    k.sel[2 + 2 * par] = (uint32_t)cnt_c;
-    k.sel[3 + 2 * par] = (uint32_t)cnt_v;
+    k.counts[0] = (uint32_t)tot_c;
+    k.counts[1] = (uint32_t)tot_v;
+    k.sel[2 + 2 * par] = (uint32_t)tot_c;
+    k.sel[3 + 2 * par] = (uint32_t)tot_v;
   }
   __syncthreads();
   if (tid == 0) {
@@ -228,8 +239,8 @@ cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int range = (k.P + 4 * sms - 1) / (4 * sms);       // about four blocks per SM
-  if (range < 4) range = 4;
+  int range = (k.P + 2 * sms - 1) / (2 * sms);      // about two blocks per SM
+  range = (range + 31) / 32 * 32;                    // whole mask words per block
   if (range > SP_MAX_RANGE) range = SP_MAX_RANGE;
   const int blocks = (k.P + range - 1) / range;
   k_select_pack<<<blocks, SP_THREADS, 0, st>>>(k, range);
@@ -256,7 +267,7 @@ __global__ void __launch_bounds__(256) k_recompute_flags(pv_dev k) {
                               : pv::color_code_of(st, at, k.state_fmt, k.color_code);
     f |= code != last[t];
   }
-  k.flags[(size_t)ch5 * k.P + p] = (uint8_t)f;
+  if (f) atomicOr(&k.chg[(vis ? k.chg_words : 0) + (p >> 5)], 1u << (p & 31));
 }
 
 }  // namespace

@@ -1,7 +1,8 @@
 // K0: per-frame blend weights of a probe volume (Section 3.2 of arXiv
 // 2103.05875, after DDGI): for every colour texel W = max(0, n_t . d_r), for
 // every visibility texel W = max(0, n_t . d_r)^sharpness, plus the weight sums
-// used for normalisation. One block per texel, threads over rays.
+// used for normalisation. One block per texel, threads over rays. Block 0
+// also clears the frame's changed-probe bits and sets the frame's hysteresis.
 //
 // Operand forms. FP32: the SIMT blend uses W as is; the tensor-core blend gets
 // W = hi + lo with hi = W truncated to TF32 and lo = W - hi (three TF32
@@ -135,6 +136,9 @@ __global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restri
   }
   if (threadIdx.x == 0) k.sums[tg] = red[0];
 
+  if (blockIdx.x == 0) {            // this frame's changed-probe bits start cleared
+    for (int w = threadIdx.x; w < 2 * k.chg_words; w += blockDim.x) k.chg[w] = 0u;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     unsigned long long f = *k.frame;
     *k.hy = (f == 0ull && k.first_frame_no_hysteresis) ? 0.0f : k.h;
