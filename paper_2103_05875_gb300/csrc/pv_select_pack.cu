@@ -182,6 +182,11 @@ __global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range)
       for (int bit = 0; bit < 32; ++bit) {
         const int p = 32 * w + bit;
         if (p >= pe) break;
+        if (p < pb) {                                  // selected probes of this word before the range
+          if ((mc >> bit) & 1u) { ++rc; lc = p; }
+          if ((mv >> bit) & 1u) { ++rv; lv = p; }
+          continue;
+        }
         const bool sc = (mc >> bit) & 1u, sv = (mv >> bit) & 1u;
         if (p >= pb) {
           slot_c[p - pb] = sc ? rc : -1;
@@ -239,9 +244,10 @@ cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int range = (k.P + 2 * sms - 1) / (2 * sms);      // about two blocks per SM
-  range = (range + 31) / 32 * 32;                    // whole mask words per block
-  if (range > SP_MAX_RANGE) range = SP_MAX_RANGE;
+  // one probe per warp keeps every probe's loads in flight at once (a warp
+  // waits one memory round trip per probe); larger volumes take several
+  int range = SP_WARPS;
+  while ((k.P + range - 1) / range > 16 * sms && range < SP_MAX_RANGE) range *= 2;
   const int blocks = (k.P + range - 1) / range;
   k_select_pack<<<blocks, SP_THREADS, 0, st>>>(k, range);
   return cudaGetLastError();
