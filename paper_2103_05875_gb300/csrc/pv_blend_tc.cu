@@ -57,7 +57,11 @@ enum Form { kF16 = 0, kBF16 = 1, kF32 = 2 };
 
 constexpr int NT = 384;
 constexpr int EPI_THREADS = 256;         // warps 4..11
-constexpr int ROWB = 64;                 // bytes per K-chunk row in shared memory
+// bytes per K-chunk row in shared memory: 64 (SWIZZLE_64B) for the 16-bit
+// forms, 32 (SWIZZLE_32B) for TF32, which keeps the FP32 form's stages small
+// enough for a four-deep ring
+template <int FORM>
+constexpr int row_bytes() { return FORM == 2 ? 32 : 64; }
 constexpr int GRP = 32;                  // rows per row group of the A tile
 constexpr int MS_LD = 129;               // odd leading dimension of the transpose buffer
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
@@ -188,16 +192,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
-// 512 bytes apart (SBO); LBO unused for this layout; descriptor version 1.
+// Shared-memory matrix descriptor: K-major rows of RB bytes with the matching
+// swizzle (64 B: SWIZZLE_64B, 32 B: SWIZZLE_32B), 8-row groups RB*8 bytes apart
+// (SBO); LBO unused for these layouts; descriptor version 1.
+template <int RB>
 __device__ __forceinline__ uint64_t sdesc(const void* p) {
   const uint64_t a = smem_u32(p);
   uint64_t d = 0;
   d |= (a & 0x3FFFFull) >> 4;            // start address
   d |= (uint64_t)1 << 16;                // leading byte offset (16 B, ignored)
-  d |= (uint64_t)(512 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)((RB * 8) >> 4) << 32;  // stride byte offset
   d |= (uint64_t)1 << 46;                // version
-  d |= (uint64_t)4 << 61;                // SWIZZLE_64B
+  d |= (uint64_t)(RB == 64 ? 4 : 6) << 61;   // SWIZZLE_64B / SWIZZLE_32B
   return d;
 }
 
@@ -237,31 +243,29 @@ struct LaneTexel {
   bool has;
 };
 
-// One pass of the fused epilogue: every probe row (ch, p) of this texture, one
-// warp per row and one texel per lane. The shared tiles are updated in place
+// One pass of the fused epilogue for a block of up to 32 texels (one per
+// lane): each warp owns a fixed share of this texture's probe rows (ch, p) and
+// loops over them, so a lane's rows are independent chains with all per-texel
+// constants in registers. Per row the shared tile is updated in place
 // (weight-sum normalisation, hysteresis, storage rounding, guard band) and the
-// row's changed flag is raised when any transmitted code differs from the
-// last-transmitted one.
+// transmitted code is compared with the last-transmitted one; changed rows are
+// collected in per-channel 32-bit probe masks, OR-reduced once per pass.
 template <int SF, int KIND, bool VIS, bool D2LO>
-__device__ __forceinline__ void epi_rows(const LaneTexel lt, const float* __restrict__ mcol, int rows, int npi,
-                                         int np, void* tiles_v, int tile_elems, const uint16_t* __restrict__ codes,
+__device__ __forceinline__ void epi_pass(const LaneTexel lt, const float* __restrict__ mcol, int npi, int np,
+                                         void* tiles_v, int tile_elems, const uint16_t* __restrict__ codes,
                                          int code_elems, float h, float omh, float d2_scale, int ew, int lane,
-                                         int* flag_s) {
+                                         uint32_t* flag_mask) {
   using ST = typename StateOps<SF>::T;
   ST* tiles = reinterpret_cast<ST*>(tiles_v);
-  constexpr int U = 4;                                 // independent rows per warp iteration
-  for (int r0 = ew; r0 < rows; r0 += 8 * U) {
-    bool changed[U];
-    int row[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int rr = r0 + 8 * u;
-      const bool live = rr < rows;
-      const int rc = live ? rr : 0;
-      const int ch = rc >= npi ? (rc >= 2 * npi ? 2 : 1) : 0;
-      const int p = rc - ch * npi;
-      row[u] = ch * GRP + p;
-      ST* tile = tiles + (ch * np + p) * tile_elems;
+  constexpr int NCH = VIS ? 2 : 3;
+  constexpr int PER = NCH * GRP / 8;                   // row slots per warp: 8 (vis), 12 (colour)
+  uint32_t m0 = 0, m1 = 0, m2 = 0;
+  if (lt.has) {
+#pragma unroll 4
+    for (int i = 0; i < PER; ++i) {
+      const int sl = ew * PER + i;
+      const int ch = sl >> 5, p = sl & 31;
+      if (p >= npi) continue;                          // uniform across the warp
       float acc;
       if (VIS) {
         acc = ch == 0 ? mcol[p] : mcol[32 + p];
@@ -269,28 +273,34 @@ __device__ __forceinline__ void epi_rows(const LaneTexel lt, const float* __rest
       } else {
         acc = mcol[32 + 32 * ch + p];
       }
-      const bool v = live && lt.has;
-      uint32_t b = v ? (uint32_t)tile[lt.pos] : 0u;
-      const uint32_t last = v ? (uint32_t)codes[(ch * np + p) * code_elems + lt.t] : 0u;
-      const uint32_t nbits = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(b), omh * (acc * lt.rS)));
-      const bool upd = v && lt.rS > 0.0f;
-      b = upd ? nbits : b;
-      if (upd) tile[lt.pos] = (ST)b;
-      if (v && lt.nb > 0) tile[lt.b0] = (ST)b;
-      if (v && lt.nb > 1) tile[lt.b1] = (ST)b;
-      if (v && lt.nb > 2) tile[lt.b2] = (ST)b;
+      ST* tile = tiles + (ch * np + p) * tile_elems;
+      uint32_t b = (uint32_t)tile[lt.pos];
+      const uint32_t last = (uint32_t)codes[(ch * np + p) * code_elems + lt.t];
+      if (lt.rS > 0.0f) {
+        b = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(b), omh * (acc * lt.rS)));
+        tile[lt.pos] = (ST)b;
+      }
+      if (lt.nb > 0) tile[lt.b0] = (ST)b;
+      if (lt.nb > 1) tile[lt.b1] = (ST)b;
+      if (lt.nb > 2) tile[lt.b2] = (ST)b;
       uint32_t code;
       if (VIS) code = SF == 0 ? b : (uint32_t)__half_as_ushort(__float2half_rn(__uint_as_float(b)));
       else if (KIND == PV_CODE_UNORM10) code = pv::unorm10_from_float(StateOps<SF>::value(b));
       else code = SF == 0 ? pv::uf10_from_half_bits(b) : pv::uf10_from_float_bits(b);
-      changed[u] = v && code != last;
+      const uint32_t bit = code != last ? (1u << p) : 0u;
+      m0 |= ch == 0 ? bit : 0u;
+      m1 |= ch == 1 ? bit : 0u;
+      m2 |= ch == 2 ? bit : 0u;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (r0 + 8 * u < rows) {                         // warp-uniform
-        if (__any_sync(0xffffffffu, changed[u]) && lane == 0) flag_s[(VIS ? 3 * GRP : 0) + row[u]] = 1;
-      }
-    }
+  }
+  m0 = __reduce_or_sync(0xffffffffu, m0);
+  m1 = __reduce_or_sync(0xffffffffu, m1);
+  if (!VIS) m2 = __reduce_or_sync(0xffffffffu, m2);
+  if (lane == 0) {
+    const int base = VIS ? 3 : 0;
+    if (m0) atomicOr(&flag_mask[base + 0], m0);
+    if (m1) atomicOr(&flag_mask[base + 1], m1);
+    if (!VIS && m2) atomicOr(&flag_mask[base + 2], m2);
   }
 }
 
@@ -326,6 +336,8 @@ __global__ void __launch_bounds__(NT, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool kSplitW = FORM != kF16;
   constexpr bool kSplitA = FORM == kF32;
+  constexpr int ROWB = row_bytes<FORM>();
+  constexpr int CPR = ROWB / 16;                   // 16-byte chunks per row
 
   uint64_t* bars = (uint64_t*)(smem + tp.off_bar);
   uint64_t* full = bars;                           // [stages]
@@ -338,7 +350,7 @@ __global__ void __launch_bounds__(NT, 1)
   float* rsum = (float*)(smem + tp.off_invs);      // [Nc + Nv]: 1 / weight sum (0: no weight)
   uint64_t* tab_border = (uint64_t*)(smem + tp.off_tab);           // [Tc + Tv]
   uint16_t* tab_pos = (uint16_t*)(tab_border + k.Tc + k.Tv);       // [Tc + Tv]
-  int* flag_s = (int*)(smem + tp.off_flags);       // [5][32]
+  uint32_t* flag_mask = (uint32_t*)(smem + tp.off_flags);   // [5]: changed probes of the item, per channel
   uint8_t* state_s = smem + tp.off_state;
   uint16_t* last_s = (uint16_t*)(smem + tp.off_last);
   float* ms = (float*)(smem + tp.off_ms);          // [32][MS_LD]: accumulators, transposed
@@ -373,7 +385,7 @@ __global__ void __launch_bounds__(NT, 1)
     tab_pos[t] = (uint16_t)((i + 1) * (n + 2) + (j + 1));
     tab_border[t] = pack_border(i, j, n);
   }
-  for (int q = threadIdx.x; q < 5 * GRP; q += NT) flag_s[q] = 0;
+  for (int q = threadIdx.x; q < 5; q += NT) flag_mask[q] = 0;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(tmem_holder))
@@ -435,23 +447,23 @@ __global__ void __launch_bounds__(NT, 1)
           tc_fence_after();
           uint8_t* st = smem + (size_t)s * tp.stage_bytes;
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {            // two 32-byte K steps per 64-byte row
+          for (int ks = 0; ks < ROWB / 32; ++ks) {     // one MMA K step per 32 bytes of row
             const int kb = ks * 32;
-            const uint64_t av = sdesc(st + kb);
-            const uint64_t ac = sdesc(st + (size_t)(tp.crow + 3 * GRP - 128) * ROWB + kb);
-            const uint64_t bv = sdesc(st + tp.off_wv + kb);
-            const uint64_t bc = sdesc(st + tp.off_wc + kb);
+            const uint64_t av = sdesc<ROWB>(st + kb);
+            const uint64_t ac = sdesc<ROWB>(st + (size_t)(tp.crow + 3 * GRP - 128) * ROWB + kb);
+            const uint64_t bv = sdesc<ROWB>(st + tp.off_wv + kb);
+            const uint64_t bc = sdesc<ROWB>(st + tp.off_wc + kb);
             const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
             mma<FORM>(dv, av, bv, tp.idesc_v, acc);
             mma<FORM>(dc, ac, bc, tp.idesc_c, acc);
             if (kSplitW) {
-              mma<FORM>(dv, av, sdesc(st + tp.off_wv_lo + kb), tp.idesc_v, 1u);
-              mma<FORM>(dc, ac, sdesc(st + tp.off_wc_lo + kb), tp.idesc_c, 1u);
+              mma<FORM>(dv, av, sdesc<ROWB>(st + tp.off_wv_lo + kb), tp.idesc_v, 1u);
+              mma<FORM>(dc, ac, sdesc<ROWB>(st + tp.off_wc_lo + kb), tp.idesc_c, 1u);
             }
             if (kSplitA) {
               uint8_t* lo = st + tp.off_a_lo;
-              mma<FORM>(dv, sdesc(lo + kb), bv, tp.idesc_v, 1u);
-              mma<FORM>(dc, sdesc(lo + (size_t)(tp.crow + 3 * GRP - 128) * ROWB + kb), bc, tp.idesc_c, 1u);
+              mma<FORM>(dv, sdesc<ROWB>(lo + kb), bv, tp.idesc_v, 1u);
+              mma<FORM>(dc, sdesc<ROWB>(lo + (size_t)(tp.crow + 3 * GRP - 128) * ROWB + kb), bc, tp.idesc_c, 1u);
             }
           }
           mma_commit(&empty[s]);                       // stage free once these MMAs finish
@@ -481,12 +493,12 @@ __global__ void __launch_bounds__(NT, 1)
         uint8_t* st = smem + (size_t)s * tp.stage_bytes;
         if constexpr (FORM == kF32) {
           // d^2 rows from full-precision d, then every row split into TF32 hi + lo
-          for (int q = ct; q < GRP * 4; q += 64) {
+          for (int q = ct; q < GRP * CPR; q += 64) {
             const float4 d = *(const float4*)(st + (size_t)q * 16);
-            *(float4*)(st + (size_t)(GRP * 4 + q) * 16) = make_float4(d.x * d.x, d.y * d.y, d.z * d.z, d.w * d.w);
+            *(float4*)(st + (size_t)(GRP * CPR + q) * 16) = make_float4(d.x * d.x, d.y * d.y, d.z * d.z, d.w * d.w);
           }
           conv_bar();
-          for (int q = ct; q < tp.a_rows * 4; q += 64) {
+          for (int q = ct; q < tp.a_rows * CPR; q += 64) {
             uint4 x = *(const uint4*)(st + (size_t)q * 16);
             uint4 hi = make_uint4(x.x & 0xFFFFE000u, x.y & 0xFFFFE000u, x.z & 0xFFFFE000u, x.w & 0xFFFFE000u);
             float4 lo = make_float4(__uint_as_float(x.x) - __uint_as_float(hi.x),
@@ -498,7 +510,7 @@ __global__ void __launch_bounds__(NT, 1)
           }
         } else {
           // d^2 = hi + lo in the operand format (binary16 scaled by 2^-8)
-          for (int q = ct; q < GRP * 4; q += 64) {
+          for (int q = ct; q < GRP * CPR; q += 64) {
             const uint4 raw = *(const uint4*)(st + (size_t)q * 16);
             const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
             uint32_t oh[4], ol[4];
@@ -530,8 +542,8 @@ __global__ void __launch_bounds__(NT, 1)
                 ol[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
               }
             }
-            *(uint4*)(st + (size_t)(GRP * 4 + q) * 16) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
-            *(uint4*)(st + (size_t)(2 * GRP * 4 + q) * 16) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+            *(uint4*)(st + (size_t)(GRP * CPR + q) * 16) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+            *(uint4*)(st + (size_t)(2 * GRP * CPR + q) * 16) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
           }
         }
         fence_proxy_async();
@@ -596,21 +608,20 @@ __global__ void __launch_bounds__(NT, 1)
         lt.rS = lt.has ? rsum[(vis ? tp.Nc : 0) + t] : 0.0f;
         lt.t = lt.has ? t : 0;
         const float* mcol = ms + lane * MS_LD;
-        const int rows = (vis ? 2 : 3) * npi;
         void* tiles = vis ? (void*)st_v : (void*)st_c;
         const int tile_elems = vis ? k.sv_stride : k.sc_stride;
         const uint16_t* codes = vis ? ls_v : ls_c;
         const int code_elems = vis ? k.lv_stride : k.lc_stride;
         const bool f16 = k.state_fmt == PV_FMT_F16;
         if (vis) {
-          if (f16) epi_rows<0, 0, true, d2_lo>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, d2_scale, ew, lane, flag_s);
-          else epi_rows<1, 0, true, d2_lo>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, d2_scale, ew, lane, flag_s);
+          if (f16) epi_pass<0, 0, true, d2_lo>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, d2_scale, ew, lane, flag_mask);
+          else epi_pass<1, 0, true, d2_lo>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, d2_scale, ew, lane, flag_mask);
         } else if (kind == PV_CODE_UNORM10) {
-          if (f16) epi_rows<0, PV_CODE_UNORM10, false, false>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_s);
-          else epi_rows<1, PV_CODE_UNORM10, false, false>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_s);
+          if (f16) epi_pass<0, PV_CODE_UNORM10, false, false>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_mask);
+          else epi_pass<1, PV_CODE_UNORM10, false, false>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_mask);
         } else {
-          if (f16) epi_rows<0, PV_CODE_UF10, false, false>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_s);
-          else epi_rows<1, PV_CODE_UF10, false, false>(lt, mcol, rows, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_s);
+          if (f16) epi_pass<0, PV_CODE_UF10, false, false>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_mask);
+          else epi_pass<1, PV_CODE_UF10, false, false>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_mask);
         }
         epi_bar();
       }
@@ -622,20 +633,14 @@ __global__ void __launch_bounds__(NT, 1)
         tph ^= 1;
       }
       if (e < 2) {                                     // changed-probe bits of this item
-        const int w0 = p0 >> 5, w1 = (p0 + npi - 1) >> 5;
-        for (int w = w0; w <= w1; ++w) {
-          uint32_t mask = 0;
-          for (int p = 0; p < npi; ++p) {
-            if (((p0 + p) >> 5) != w) continue;
-            const int f = e == 0 ? (flag_s[p] | flag_s[GRP + p] | flag_s[2 * GRP + p])
-                                 : (flag_s[3 * GRP + p] | flag_s[4 * GRP + p]);
-            if (f) mask |= 1u << ((p0 + p) & 31);
-          }
-          if (mask) atomicOr(&k.chg[e * k.chg_words + w], mask);
-        }
+        const uint32_t m = e == 0 ? (flag_mask[0] | flag_mask[1] | flag_mask[2]) : (flag_mask[3] | flag_mask[4]);
+        const int sh = p0 & 31;
+        uint32_t* w = &k.chg[e * k.chg_words + (p0 >> 5)];
+        if (m << sh) atomicOr(w, m << sh);
+        if (sh && (m >> (32 - sh))) atomicOr(w + 1, m >> (32 - sh));
       }
       epi_bar();
-      for (int q = e; q < 5 * GRP; q += EPI_THREADS) flag_s[q] = 0;
+      if (e < 5) flag_mask[e] = 0;
       fence_proxy_async();
       epi_bar();
       if (e == 0) {
@@ -692,12 +697,14 @@ CUtensorMapDataType dtype_of(int fmt) {
 
 cudaError_t encode_2d(CUtensorMap* m, int fmt, const void* base, uint64_t inner, uint64_t rows,
                       uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows) {
+  const CUtensorMapSwizzle swz = box_inner * (fmt == PV_FMT_F32 ? 4u : 2u) == 64u ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                                                : CU_TENSOR_MAP_SWIZZLE_32B;
   cuuint64_t dims[2] = {inner, rows};
   cuuint64_t strides[1] = {row_bytes};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = g_encode(m, dtype_of(fmt), 2, const_cast<void*>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -762,6 +769,7 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   tp.np = np;
   tp.items = (k.P + np - 1) / np;
   pl->grid = tp.items < sms ? tp.items : sms;
+  const int ROWB = form == kF32 ? row_bytes<kF32>() : row_bytes<kF16>();
   tp.kc = ROWB / ob;
   tp.nchunks = (k.R + tp.kc - 1) / tp.kc;
   tp.Nc = k.tc_pad;
