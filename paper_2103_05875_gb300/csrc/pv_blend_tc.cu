@@ -61,7 +61,7 @@ constexpr int EPI_THREADS = 256;         // warps 4..11
 // forms, 32 (SWIZZLE_32B) for TF32, which keeps the FP32 form's stages small
 // enough for a four-deep ring
 template <int FORM>
-constexpr int row_bytes() { return FORM == 2 ? 32 : 64; }
+__host__ __device__ constexpr int row_bytes() { return FORM == 2 ? 32 : 64; }
 constexpr int GRP = 32;                  // rows per row group of the A tile
 constexpr int MS_LD = 129;               // odd leading dimension of the transpose buffer
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
@@ -256,41 +256,64 @@ __device__ __forceinline__ void epi_pass(const LaneTexel lt, const float* __rest
                                          int code_elems, float h, float omh, float d2_scale, int ew, int lane,
                                          uint32_t* flag_mask) {
   using ST = typename StateOps<SF>::T;
-  ST* tiles = reinterpret_cast<ST*>(tiles_v);
+  ST* __restrict__ tiles = reinterpret_cast<ST*>(tiles_v);
   constexpr int NCH = VIS ? 2 : 3;
   constexpr int PER = NCH * GRP / 8;                   // row slots per warp: 8 (vis), 12 (colour)
+  constexpr int U = 4;                                 // rows in flight per lane
   uint32_t m0 = 0, m1 = 0, m2 = 0;
-  if (lt.has) {
-#pragma unroll 4
-    for (int i = 0; i < PER; ++i) {
-      const int sl = ew * PER + i;
+#pragma unroll
+  for (int i0 = 0; i0 < PER; i0 += U) {
+    // all loads of U rows first (branch-free), so the rows' chains overlap
+    float acc[U];
+    uint32_t old[U], last[U];
+    int off[U], chs[U], ps[U];
+    bool live[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int sl = ew * PER + i0 + u;
       const int ch = sl >> 5, p = sl & 31;
-      if (p >= npi) continue;                          // uniform across the warp
-      float acc;
+      live[u] = lt.has && p < npi;
+      chs[u] = ch;
+      ps[u] = p;
+      const int pc = live[u] ? p : 0;
+      off[u] = (ch * np + pc) * tile_elems;
+      float a;
       if (VIS) {
-        acc = ch == 0 ? mcol[p] : mcol[32 + p];
-        if (ch == 1) acc = (D2LO ? acc + mcol[64 + p] : acc) * d2_scale;
+        a = ch == 0 ? mcol[pc] : mcol[32 + pc];
+        if (ch == 1) a = (D2LO ? a + mcol[64 + pc] : a) * d2_scale;
       } else {
-        acc = mcol[32 + 32 * ch + p];
+        a = mcol[32 + 32 * ch + pc];
       }
-      ST* tile = tiles + (ch * np + p) * tile_elems;
-      uint32_t b = (uint32_t)tile[lt.pos];
-      const uint32_t last = (uint32_t)codes[(ch * np + p) * code_elems + lt.t];
-      if (lt.rS > 0.0f) {
-        b = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(b), omh * (acc * lt.rS)));
-        tile[lt.pos] = (ST)b;
+      acc[u] = a;
+      old[u] = (uint32_t)tiles[off[u] + lt.pos];
+      last[u] = (uint32_t)codes[(ch * np + pc) * code_elems + lt.t];
+    }
+    // math, then stores
+    uint32_t nb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t upd = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(old[u]), omh * (acc[u] * lt.rS)));
+      nb[u] = lt.rS > 0.0f ? upd : old[u];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (live[u]) {
+        tiles[off[u] + lt.pos] = (ST)nb[u];
+        if (lt.nb > 0) tiles[off[u] + lt.b0] = (ST)nb[u];
+        if (lt.nb > 1) tiles[off[u] + lt.b1] = (ST)nb[u];
+        if (lt.nb > 2) tiles[off[u] + lt.b2] = (ST)nb[u];
       }
-      if (lt.nb > 0) tile[lt.b0] = (ST)b;
-      if (lt.nb > 1) tile[lt.b1] = (ST)b;
-      if (lt.nb > 2) tile[lt.b2] = (ST)b;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
       uint32_t code;
-      if (VIS) code = SF == 0 ? b : (uint32_t)__half_as_ushort(__float2half_rn(__uint_as_float(b)));
-      else if (KIND == PV_CODE_UNORM10) code = pv::unorm10_from_float(StateOps<SF>::value(b));
-      else code = SF == 0 ? pv::uf10_from_half_bits(b) : pv::uf10_from_float_bits(b);
-      const uint32_t bit = code != last ? (1u << p) : 0u;
-      m0 |= ch == 0 ? bit : 0u;
-      m1 |= ch == 1 ? bit : 0u;
-      m2 |= ch == 2 ? bit : 0u;
+      if (VIS) code = SF == 0 ? nb[u] : (uint32_t)__half_as_ushort(__float2half_rn(__uint_as_float(nb[u])));
+      else if (KIND == PV_CODE_UNORM10) code = pv::unorm10_from_float(StateOps<SF>::value(nb[u]));
+      else code = SF == 0 ? pv::uf10_from_half_bits(nb[u]) : pv::uf10_from_float_bits(nb[u]);
+      const uint32_t bit = (live[u] && code != last[u]) ? (1u << ps[u]) : 0u;
+      m0 |= chs[u] == 0 ? bit : 0u;
+      m1 |= chs[u] == 1 ? bit : 0u;
+      m2 |= chs[u] == 2 ? bit : 0u;
     }
   }
   m0 = __reduce_or_sync(0xffffffffu, m0);
@@ -492,21 +515,31 @@ __global__ void __launch_bounds__(NT, 1)
         if (!ok) break;
         uint8_t* st = smem + (size_t)s * tp.stage_bytes;
         if constexpr (FORM == kF32) {
-          // d^2 rows from full-precision d, then every row split into TF32 hi + lo
-          for (int q = ct; q < GRP * CPR; q += 64) {
-            const float4 d = *(const float4*)(st + (size_t)q * 16);
-            *(float4*)(st + (size_t)(GRP * CPR + q) * 16) = make_float4(d.x * d.x, d.y * d.y, d.z * d.z, d.w * d.w);
-          }
+          // d^2 rows from full-precision d, then every row split into TF32 hi + lo;
+          // each thread loads all of its chunks before it stores any
+          constexpr int DCH = GRP * CPR / 64;          // d chunks per thread
+          float4 d[DCH];
+#pragma unroll
+          for (int u = 0; u < DCH; ++u) d[u] = *(const float4*)(st + (size_t)(ct + 64 * u) * 16);
+#pragma unroll
+          for (int u = 0; u < DCH; ++u)
+            *(float4*)(st + (size_t)(GRP * CPR + ct + 64 * u) * 16) =
+                make_float4(d[u].x * d[u].x, d[u].y * d[u].y, d[u].z * d[u].z, d[u].w * d[u].w);
           conv_bar();
-          for (int q = ct; q < tp.a_rows * CPR; q += 64) {
-            uint4 x = *(const uint4*)(st + (size_t)q * 16);
-            uint4 hi = make_uint4(x.x & 0xFFFFE000u, x.y & 0xFFFFE000u, x.z & 0xFFFFE000u, x.w & 0xFFFFE000u);
-            float4 lo = make_float4(__uint_as_float(x.x) - __uint_as_float(hi.x),
-                                    __uint_as_float(x.y) - __uint_as_float(hi.y),
-                                    __uint_as_float(x.z) - __uint_as_float(hi.z),
-                                    __uint_as_float(x.w) - __uint_as_float(hi.w));
-            *(uint4*)(st + (size_t)q * 16) = hi;
-            *(float4*)(st + tp.off_a_lo + (size_t)q * 16) = lo;
+          constexpr int ACH = 160 * CPR / 64;          // chunks per thread over the A tile's 160 rows
+          uint4 x[ACH];
+#pragma unroll
+          for (int u = 0; u < ACH; ++u) x[u] = *(const uint4*)(st + (size_t)(ct + 64 * u) * 16);
+#pragma unroll
+          for (int u = 0; u < ACH; ++u) {
+            const uint4 hi = make_uint4(x[u].x & 0xFFFFE000u, x[u].y & 0xFFFFE000u, x[u].z & 0xFFFFE000u,
+                                        x[u].w & 0xFFFFE000u);
+            const float4 lo = make_float4(__uint_as_float(x[u].x) - __uint_as_float(hi.x),
+                                          __uint_as_float(x[u].y) - __uint_as_float(hi.y),
+                                          __uint_as_float(x[u].z) - __uint_as_float(hi.z),
+                                          __uint_as_float(x[u].w) - __uint_as_float(hi.w));
+            *(uint4*)(st + (size_t)(ct + 64 * u) * 16) = hi;
+            *(float4*)(st + tp.off_a_lo + (size_t)(ct + 64 * u) * 16) = lo;
           }
         } else {
           // d^2 = hi + lo in the operand format (binary16 scaled by 2^-8)
