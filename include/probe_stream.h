@@ -226,6 +226,35 @@ pv_status probe_volume_import_state(pv_volume* vol, const void* tiles_c, const v
                                     const uint16_t* last_c, const uint16_t* last_v,
                                     uint64_t frame, void* stream);
 
+/*
+ * Allocation-free variant of probe_update (no counterpart in the paper): for
+ * callers that cannot allocate device memory -- code running where cudaMalloc
+ * is unavailable or not allowed, such as a stream callback, a graph host node,
+ * or a plugin confined to memory its host application owns. It runs the
+ * weights kernel and the SIMT blend kernel on caller buffers; its only scratch
+ * (the frame's weights and their sums) is a file-scope device array of
+ * PV_STATIC_SCRATCH_BYTES per GPU, held until the process exits.
+ *  desc      volume descriptor (validated as by probe_volume_create).
+ *  frame     number of updates the state has seen (0 on the first call; only
+ *            first_frame_no_hysteresis looks at it).
+ *  radiance, dist, dirs   device inputs as for probe_update.
+ *  tiles_c, tiles_v       device state, read and written in place, layouts as
+ *            above (unpadded tiles).
+ *  last_c, last_v         device last-transmitted codes (read only).
+ *  changed_bits           device output [2][ceil(P/32)] uint32: bit p%32 of word
+ *            p/32 is set when probe p's colour (first half) or visibility
+ *            (second half) codes differ from the last-transmitted ones.
+ * Errors: PV_ERR_INVALID (NULL or bad field), PV_ERR_RANGE when
+ * rays * (n_c^2 + n_v^2) exceeds what the scratch array holds (about 262000
+ * weights), PV_ERR_CUDA. Asynchronous on `stream`. The first call on a device
+ * looks up the array's device address, so make it before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race.
+ */
+#define PV_STATIC_SCRATCH_BYTES (1u << 20)
+pv_status probe_update_static(const pv_desc* desc, uint64_t frame, const void* radiance, const void* dist,
+                              const float* dirs, void* tiles_c, void* tiles_v, const uint16_t* last_c,
+                              const uint16_t* last_v, uint32_t* changed_bits, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,7 @@ def _load():
         "probe_frame_download": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "probe_volume_export_state": (i32, [vp, vp, vp, vp, vp, C.POINTER(u64), vp]),
         "probe_volume_import_state": (i32, [vp, vp, vp, vp, vp, u64, vp]),
+        "probe_update_static": (i32, [C.POINTER(pv_desc), u64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -218,6 +219,14 @@ def probe_volume_import_state(vol: int, tiles_c, tiles_v, last_c, last_v, frame:
     _check(lib.probe_volume_import_state(vol, _ptr(tiles_c), _ptr(tiles_v), _ptr(last_c),
                                          _ptr(last_v), int(frame), _stream(stream)),
            "probe_volume_import_state")
+
+
+def probe_update_static(desc: pv_desc, frame: int, radiance, dist, dirs, tiles_c, tiles_v, last_c, last_v,
+                        changed_bits, stream=None):
+    """Allocation-free update on caller buffers (see include/probe_stream.h)."""
+    _check(lib.probe_update_static(C.byref(desc), int(frame), _ptr(radiance), _ptr(dist), _ptr(dirs),
+                                   _ptr(tiles_c), _ptr(tiles_v), _ptr(last_c), _ptr(last_v),
+                                   _ptr(changed_bits), _stream(stream)), "probe_update_static")
 
 
 # ------------------------------------------------------------------ device views
