@@ -2,19 +2,22 @@
 // a tcgen05 contraction with a fused epilogue, for sm_103a.
 //
 // The blend is a dense contraction because every probe of a volume shares the
-// frame's ray directions: per probe row x (a colour channel, d or d^2) and
-// texel t, acc[t] = sum_r W[t, r] x[r]. Rows of a work item (np <= 32 probes)
-// form the MMA's M dimension, texels its N dimension, rays its K dimension:
+// frame's ray directions: per texel t and probe row x (a colour channel, d or
+// d^2), acc[t, x] = sum_r W[t, r] x[r]. Texels form the MMA's M dimension (one
+// tensor-memory lane per texel, 128-texel tiles), the probe rows of a work
+// item (np <= 32 probes per row group) its N dimension, rays its K dimension:
 //
-//   A (shared memory, K-major, 64-byte rows, SWIZZLE_64B), row groups of 32:
+//   A (shared memory, K-major): the weight tiles W_c [Tc x K] and W_v [Tv x K]
+//     from the weights kernel. Rows past the texture's texels are never
+//     loaded; the lanes they produce are ignored.
+//   B (shared memory, K-major, one row per probe row, row groups of 32):
 //     [ d | d^2 (hi) | d^2 lo (16-bit forms) | R | G | B ]
 //     d and the colour planes come straight from HBM by TMA; d^2 is formed on
 //     chip by two converter warps (its rounding to the operand format is split
 //     into hi + lo parts so that it costs no accuracy).
-//   B (shared memory): W_v [Nv x K] and W_c [Nc x K] from the weights kernel.
-//   D (tensor memory, FP32): vis MMA over A rows 0..127 with N = Nv, colour
-//     MMA over the 128 rows that end with the B plane, N = Nc. Accumulator
-//     lanes: vis d = 0..31, d^2 = 32..63 (+64..95 lo); colour R, G, B = 32..127.
+//   D (tensor memory, FP32), per 128-texel tile: visibility N = 64 columns
+//     (d, d^2; the d^2 lo rows accumulate into the d^2 columns with N = 32),
+//     colour N = 96 columns (R, G, B).
 //
 // Operand forms (pv_desc.operand_fmt):
 //   F16  kind::f16, binary16 inputs; visibility weights scaled by 2^15 and
@@ -25,19 +28,23 @@
 //        TF32 parts, three MMAs (hi*hi + hi*lo + lo*hi) recover float32
 //        accuracy.
 //
-// Warp roles (384 threads, one CTA per SM, persistent over work items):
+// Warp roles (512 threads, one CTA per SM, persistent over work items):
 //   warp 0     TMA producer: ray tiles and weight tiles into a ring of stages;
-//              the item's old texels and last-transmitted codes (bulk copies)
 //   warp 1     TMEM allocation and the single MMA-issuing thread
 //   warps 2-3  converters: d^2 rows, TF32 hi/lo split
-//   warps 4-11 epilogue: TMEM -> registers -> shared (transposed), then the
-//              fused per-texel work of Sections 3.2-3.4 (weight-sum
-//              normalisation, hysteresis, storage rounding, guard band,
-//              transmitted code, comparison with the last-transmitted code,
-//              changed flags) on the item's tiles in shared memory, one probe
-//              row per warp and one texel per lane, written back by bulk copies.
-// Accumulators are double-buffered in TMEM when both fit in 256 columns, so
-// an item's epilogue overlaps the next item's MMAs. Every mbarrier wait is
+//   warps 4-15 epilogue. A lane owns one texel (its TMEM lane) and a task is
+//              one 32-column load: 32 probe rows of one channel of that texel.
+//              Per row the fused work of Sections 3.2-3.4 runs with every
+//              per-texel constant in registers (weight-sum normalisation,
+//              hysteresis, storage rounding, transmitted code, comparison with
+//              the last-transmitted code, changed flags) on the item's tiles in
+//              shared memory; the guard band is copied afterwards for all rows,
+//              and the tiles go back to HBM by bulk copies. The item's old
+//              texels and codes are streamed in by bulk copies while the
+//              previous item is still being processed.
+// Accumulators are double-buffered in TMEM (columns 0 and 256) when a buffer
+// needs at most 256 columns, so an item's epilogue overlaps the next item's
+// MMAs. Every mbarrier wait is
 // bounded in time; on expiry the kernel raises the volume's error word and
 // every role leaves its loop, so no wait can hang the GPU.
 #include <cuda.h>
@@ -55,27 +62,29 @@ namespace {
 
 enum Form { kF16 = 0, kBF16 = 1, kF32 = 2 };
 
-constexpr int NT = 384;
-constexpr int EPI_THREADS = 256;         // warps 4..11
+constexpr int NT = 512;
+constexpr int EPI_WARPS = 12;            // warps 4..15, three per TMEM lane quarter
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
 // bytes per K-chunk row in shared memory: 64 (SWIZZLE_64B) for the 16-bit
 // forms, 32 (SWIZZLE_32B) for TF32, which keeps the FP32 form's stages small
 // enough for a four-deep ring
 template <int FORM>
 __host__ __device__ constexpr int row_bytes() { return FORM == 2 ? 32 : 64; }
-constexpr int GRP = 32;                  // rows per row group of the A tile
-constexpr int MS_LD = 129;               // odd leading dimension of the transpose buffer
+constexpr int GRP = 32;                  // probe rows per row group of the B tile
+constexpr int MT = 128;                  // texels per MMA tile (M)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 
 struct TcParams {
   pv_dev k;
   int np, items, stages, kc, nchunks;
-  int Nc, Nv, nbuf, col_v, col_c;
-  int crow;                              // first A row of the colour block
-  int a_rows;                            // rows of the A tile
+  int ntc, ntv, bufcols, nbuf;           // 128-texel tiles per texture; TMEM columns a buffer uses
+  int crow;                              // first B row of the colour block
+  int a_rows;                            // rows of the ray (B) tile
   int off_a_lo, off_wc, off_wc_lo, off_wv, off_wv_lo, stage_bytes;
-  int off_state, off_last, off_ms, off_invs, off_flags, off_bar, off_tab;
+  int off_state, off_last, off_rsum, off_pos, off_gb, off_flags, off_bar;
+  int gb_c, gb_v;                        // guard-band texels per tile: 4n + 4
   uint32_t stage_tx;
-  uint32_t idesc_c, idesc_v;
+  uint32_t idesc32, idesc64, idesc96;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -126,7 +135,7 @@ __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 384;" ::: "memory"); }
 __device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 2, 64;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -178,19 +187,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                    smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-      " [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15])
-      : "r"(taddr));
+// 8 consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major rows of RB bytes with the matching
 // swizzle (64 B: SWIZZLE_64B, 32 B: SWIZZLE_32B), 8-row groups RB*8 bytes apart
@@ -207,25 +213,11 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
   return d;
 }
 
-// ------------------------------------------------------------------ epilogue texel
-// Per-texel constants of the epilogue, built once per launch: the texel's
-// position in its tile and the guard-band positions that copy it (at most
-// three for n >= 2, packed 16 bits each, count in the top 16 bits).
-__device__ __forceinline__ uint64_t pack_border(int i, int j, int n) {
-  int tr[8], tc[8];
-  const int nb = pv::border_targets(i, j, n, tr, tc);
-  uint64_t v = 0;
-  int m = nb < 3 ? nb : 3;
-  for (int b = 0; b < m; ++b) v |= (uint64_t)(tr[b] * (n + 2) + tc[b]) << (16 * b);
-  return v | ((uint64_t)m << 48);
-}
-
-// State format as a compile-time choice: 0 binary16, 1 binary32. Tiles are
-// addressed in elements through typed shared-memory pointers so the compiler
-// can schedule the epilogue's loads and stores freely.
+// ------------------------------------------------------------------ epilogue
+// State format as a compile-time choice: 0 binary16, 1 binary32.
 template <int SF>
 struct StateOps {
-  using T = typename std::conditional<SF == 0, uint16_t, uint32_t>::type;
+  static constexpr int SB = SF == 0 ? 2 : 4;         // bytes per stored texel
   static __device__ __forceinline__ float value(uint32_t b) {
     return SF == 0 ? __half2float(__ushort_as_half((unsigned short)b)) : __uint_as_float(b);
   }
@@ -234,97 +226,122 @@ struct StateOps {
   }
 };
 
-// Per-lane constants of the texel a lane handles in an epilogue pass.
-struct LaneTexel {
-  uint32_t pos, b0, b1, b2;   // element offsets in the tile: the texel and its guard-band copies
-  int nb;                     // number of guard-band copies (0 for lanes without a texel)
-  float rS;                   // 1 / weight sum (0: no weight, the texel keeps its value)
-  int t;                      // texel index (code offset in a code row)
-  bool has;
-};
+// Shared-memory loads and stores of 2- or 4-byte elements at 32-bit shared
+// addresses.
+template <int B>
+__device__ __forceinline__ uint32_t lds(uint32_t a) {
+  uint32_t v;
+  if constexpr (B == 2) asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a));
+  else asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+// Store only where `on` is set. The predicate lives inside the instruction,
+// so a row's store does not split the surrounding code into branches and the
+// rows of a group stay free to overlap.
+template <int B>
+__device__ __forceinline__ void sts_if(bool on, uint32_t a, uint32_t v) {
+  if constexpr (B == 2)
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.shared.u16 [%0], %1;\n}\n" ::"r"(a),
+                 "h"((unsigned short)v), "r"((uint32_t)on));
+  else
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.shared.u32 [%0], %1;\n}\n" ::"r"(a), "r"(v),
+                 "r"((uint32_t)on));
+}
 
-// One pass of the fused epilogue for a block of up to 32 texels (one per
-// lane): each warp owns a fixed share of this texture's probe rows (ch, p) and
-// loops over them, so a lane's rows are independent chains with all per-texel
-// constants in registers. Per row the shared tile is updated in place
-// (weight-sum normalisation, hysteresis, storage rounding, guard band) and the
-// transmitted code is compared with the last-transmitted one; changed rows are
-// collected in per-channel 32-bit probe masks, OR-reduced once per pass.
-template <int SF, int KIND, bool VIS, bool D2LO>
-__device__ __forceinline__ void epi_pass(const LaneTexel lt, const float* __restrict__ mcol, int npi, int np,
-                                         void* tiles_v, int tile_elems, const uint16_t* __restrict__ codes,
-                                         int code_elems, float h, float omh, float d2_scale, int ew, int lane,
-                                         uint32_t* flag_mask) {
-  using ST = typename StateOps<SF>::T;
-  ST* __restrict__ tiles = reinterpret_cast<ST*>(tiles_v);
-  constexpr int NCH = VIS ? 2 : 3;
-  constexpr int PER = NCH * GRP / 8;                   // row slots per warp: 8 (vis), 12 (colour)
-  constexpr int U = 4;                                 // rows in flight per lane
-  uint32_t m0 = 0, m1 = 0, m2 = 0;
+// Transmitted code of a stored texel (Section 3.4): visibility as binary16
+// bits, colour as UF10 or UNORM10.
+template <int SF, int KIND, bool VIS>
+__device__ __forceinline__ uint32_t texel_code(uint32_t b) {
+  if (VIS) return SF == 0 ? b : (uint32_t)__half_as_ushort(__float2half_rn(__uint_as_float(b)));
+  if (KIND == PV_CODE_UNORM10) return pv::unorm10_from_float(StateOps<SF>::value(b));
+  return SF == 0 ? pv::uf10_from_half_bits(b) : pv::uf10_from_float_bits(b);
+}
+
+// One epilogue task: the 32 accumulator columns at taddr are probe rows
+// p = 0..31 of one channel, and this lane's TMEM lane is one texel, whose
+// stored value in row p sits at s_tile + p * row_b and whose last-transmitted
+// code at s_code + p * code_b (shared addresses). Rows go in groups of U: one
+// TMEM load per group, then the group's old texels and last codes, then the
+// arithmetic and stores. The group loop stays rolled so that the epilogue's
+// code is small enough to stay in the instruction cache. Returns the rows
+// whose transmitted code changed as a bit mask (bit p).
+template <int SF, int KIND, bool VIS>
+__device__ __forceinline__ uint32_t epi_task(uint32_t taddr, bool has, uint32_t s_tile, uint32_t s_code, float rS,
+                                             float h, float omh, float scale, uint32_t row_b, uint32_t code_b,
+                                             int npi) {
+  constexpr int SB = StateOps<SF>::SB;
+  constexpr int U = 8;
+  const float c = omh * (rS * scale);
+  const bool upd = rS > 0.0f;
+  uint32_t ro[U], co[U];                             // row offsets within a group
 #pragma unroll
-  for (int i0 = 0; i0 < PER; i0 += U) {
-    // all loads of U rows first (branch-free), so the rows' chains overlap
-    float acc[U];
+  for (int u = 0; u < U; ++u) {
+    ro[u] = (uint32_t)u * row_b;
+    co[u] = (uint32_t)u * code_b;
+  }
+  uint32_t m = 0;
+#pragma unroll 1
+  for (int g = 0; g < npi; g += U) {
+    float v[U];
+    tmem_ld8(taddr + (uint32_t)g, v);
+    const uint32_t tb = s_tile + (uint32_t)g * row_b, cb = s_code + (uint32_t)g * code_b;
+    // rows of this group inside the item (none for lanes without a texel);
+    // rows past the item still load (the shared regions are padded for it)
+    const int lim = has ? npi - g : 0;
     uint32_t old[U], last[U];
-    int off[U], chs[U], ps[U];
-    bool live[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int sl = ew * PER + i0 + u;
-      const int ch = sl >> 5, p = sl & 31;
-      live[u] = lt.has && p < npi;
-      chs[u] = ch;
-      ps[u] = p;
-      const int pc = live[u] ? p : 0;
-      off[u] = (ch * np + pc) * tile_elems;
-      float a;
-      if (VIS) {
-        a = ch == 0 ? mcol[pc] : mcol[32 + pc];
-        if (ch == 1) a = (D2LO ? a + mcol[64 + pc] : a) * d2_scale;
-      } else {
-        a = mcol[32 + 32 * ch + pc];
-      }
-      acc[u] = a;
-      old[u] = (uint32_t)tiles[off[u] + lt.pos];
-      last[u] = (uint32_t)codes[(ch * np + pc) * code_elems + lt.t];
+      old[u] = lds<SB>(tb + ro[u]);
+      last[u] = lds<2>(cb + co[u]);
     }
-    // math, then stores
-    uint32_t nb[U];
+    uint32_t mg = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint32_t upd = StateOps<SF>::bits(fmaf(h, StateOps<SF>::value(old[u]), omh * (acc[u] * lt.rS)));
-      nb[u] = lt.rS > 0.0f ? upd : old[u];
+      const bool live = u < lim;
+      const float nv = fmaf(h, StateOps<SF>::value(old[u]), v[u] * c);
+      const uint32_t nb = upd ? StateOps<SF>::bits(nv) : old[u];
+      sts_if<SB>(live, tb + ro[u], nb);
+      const uint32_t code = texel_code<SF, KIND, VIS>(nb);
+      mg |= (live && code != last[u]) ? (1u << u) : 0u;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (live[u]) {
-        tiles[off[u] + lt.pos] = (ST)nb[u];
-        if (lt.nb > 0) tiles[off[u] + lt.b0] = (ST)nb[u];
-        if (lt.nb > 1) tiles[off[u] + lt.b1] = (ST)nb[u];
-        if (lt.nb > 2) tiles[off[u] + lt.b2] = (ST)nb[u];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      uint32_t code;
-      if (VIS) code = SF == 0 ? nb[u] : (uint32_t)__half_as_ushort(__float2half_rn(__uint_as_float(nb[u])));
-      else if (KIND == PV_CODE_UNORM10) code = pv::unorm10_from_float(StateOps<SF>::value(nb[u]));
-      else code = SF == 0 ? pv::uf10_from_half_bits(nb[u]) : pv::uf10_from_float_bits(nb[u]);
-      const uint32_t bit = (live[u] && code != last[u]) ? (1u << ps[u]) : 0u;
-      m0 |= chs[u] == 0 ? bit : 0u;
-      m1 |= chs[u] == 1 ? bit : 0u;
-      m2 |= chs[u] == 2 ? bit : 0u;
+    m |= mg << g;
+  }
+  return m;
+}
+
+// All tasks of one texture in one TMEM buffer for this warp: tiles j of 128
+// texels, this warp's lane quarter, channels ch; the tasks of a quarter are
+// dealt round-robin to its three warps.
+template <int SF, int KIND, bool VIS>
+__device__ __forceinline__ uint32_t epi_texture(uint32_t tcol, int ntiles, int T, int quarter, int slot, int lane,
+                                                int& task, uint32_t s_rsum, uint32_t s_pos,
+                                                uint32_t s_tiles, int tile_elems, uint32_t s_codes, int code_elems,
+                                                int np, int npi, float h, float omh, float d2_scale) {
+  constexpr int NCH = VIS ? 2 : 3;
+  constexpr int CW = VIS ? 64 : 96;                  // TMEM columns per tile
+  constexpr int SB = StateOps<SF>::SB;
+  const uint32_t row_b = (uint32_t)tile_elems * SB, code_b = (uint32_t)code_elems * 2;
+  uint32_t m = 0;
+  for (int j = 0; j < ntiles; ++j) {
+    const int t0 = MT * j + GRP * quarter;
+    if (t0 >= T) continue;
+    const int t = t0 + lane;
+    const bool has = t < T;
+    const int tt = has ? t : t0;
+    const float rS = has ? __uint_as_float(lds<4>(s_rsum + 4u * tt)) : 0.0f;
+    const uint32_t pos = lds<2>(s_pos + 2u * tt);
+#pragma unroll 1
+    for (int ch = 0; ch < NCH; ++ch) {
+      const int mine = task++ % 3;
+      if (mine != slot) continue;
+      const float scale = (VIS && ch == 1) ? d2_scale : 1.0f;
+      m |= epi_task<SF, KIND, VIS>(tcol + CW * j + GRP * ch, has,
+                                   s_tiles + (uint32_t)(ch * np) * row_b + pos * SB,
+                                   s_codes + (uint32_t)(ch * np) * code_b + (uint32_t)tt * 2, rS, h, omh, scale,
+                                   row_b, code_b, npi);
     }
   }
-  m0 = __reduce_or_sync(0xffffffffu, m0);
-  m1 = __reduce_or_sync(0xffffffffu, m1);
-  if (!VIS) m2 = __reduce_or_sync(0xffffffffu, m2);
-  if (lane == 0) {
-    const int base = VIS ? 3 : 0;
-    if (m0) atomicOr(&flag_mask[base + 0], m0);
-    if (m1) atomicOr(&flag_mask[base + 1], m1);
-    if (!VIS && m2) atomicOr(&flag_mask[base + 2], m2);
-  }
+  return m;
 }
 
 // The item's old texels and last-transmitted codes, into shared memory.
@@ -344,6 +361,48 @@ __device__ __forceinline__ void prefetch_item(const pv_dev& k, int np, int p0, i
              (const uint8_t*)k.state_v + ((size_t)c * k.P + p0) * k.sv_stride * sb, sv_b, bar);
     bulk_g2s(ls_v + (size_t)c * np * k.lv_stride, k.last_v + ((size_t)c * k.P + p0) * k.lv_stride, lv_b, bar);
   }
+}
+
+// Guard band (Section 3.3) of every row of an item, from the interior texels
+// just written. A lane keeps its guard-band table entries in registers; the
+// epilogue warps share the rows, four rows in flight per lane.
+template <int SF>
+__device__ __forceinline__ void guard_band(uint32_t s_base, uint32_t s_g, int ng, int nch, int tile_elems,
+                                           int np, int npi, int ew, int lane) {
+  constexpr int SB = StateOps<SF>::SB;
+  const uint32_t row_b = (uint32_t)tile_elems * SB;
+  for (int q0 = 0; q0 < ng; q0 += 32) {
+    const int q = q0 + lane;
+    const bool ok = q < ng;
+    const uint32_t ent = ok ? lds<4>(s_g + 4u * q) : 0u;
+    const uint32_t dst = (ent & 0xFFFFu) * SB, src = (ent >> 16) * SB;
+    for (int ch = 0; ch < nch; ++ch) {
+      const uint32_t rb = s_base + (uint32_t)(ch * np) * row_b;
+      for (int p0 = ew; p0 < npi; p0 += 4 * EPI_WARPS) {
+        uint32_t val[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int p = p0 + u * EPI_WARPS;
+          const uint32_t r = rb + (uint32_t)(p < npi ? p : p0) * row_b;
+          val[u] = lds<SB>(r + src);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int p = p0 + u * EPI_WARPS;
+          sts_if<SB>(ok && p < npi, rb + (uint32_t)p * row_b + dst, val[u]);
+        }
+      }
+    }
+  }
+}
+
+// Guard-band table slot of border position (r, c) of an (n+2)^2 tile: the
+// ring in the order top row, bottom row, left column, right column.
+__device__ __forceinline__ int ring_slot(int r, int c, int n) {
+  if (r == 0) return c;
+  if (r == n + 1) return (n + 2) + c;
+  if (c == 0) return 2 * (n + 2) + (r - 1);
+  return 2 * (n + 2) + n + (r - 1);
 }
 
 // ------------------------------------------------------------------ kernel
@@ -370,13 +429,12 @@ __global__ void __launch_bounds__(NT, 1)
   uint64_t* tempty = tfull + 2;                    // [2]
   uint64_t* efull = tempty + 2;                    // [1]: an item's texels and codes arrived
   uint32_t* tmem_holder = (uint32_t*)(efull + 1);
-  float* rsum = (float*)(smem + tp.off_invs);      // [Nc + Nv]: 1 / weight sum (0: no weight)
-  uint64_t* tab_border = (uint64_t*)(smem + tp.off_tab);           // [Tc + Tv]
-  uint16_t* tab_pos = (uint16_t*)(tab_border + k.Tc + k.Tv);       // [Tc + Tv]
-  uint32_t* flag_mask = (uint32_t*)(smem + tp.off_flags);   // [5]: changed probes of the item, per channel
+  float* rsum = (float*)(smem + tp.off_rsum);      // [Tc + Tv]: 1 / weight sum (0: no weight)
+  uint16_t* tab_pos = (uint16_t*)(smem + tp.off_pos);   // [Tc + Tv]: texel position in its tile
+  uint32_t* gb = (uint32_t*)(smem + tp.off_gb);    // [gb_c + gb_v]: guard-band dst | src << 16
+  uint32_t* flag_mask = (uint32_t*)(smem + tp.off_flags);   // [2][2]: changed probes, by item parity
   uint8_t* state_s = smem + tp.off_state;
   uint16_t* last_s = (uint16_t*)(smem + tp.off_last);
-  float* ms = (float*)(smem + tp.off_ms);          // [32][MS_LD]: accumulators, transposed
 
   const int sb = k.state_fmt == PV_FMT_F16 ? 2 : 4;
   const int np = tp.np;
@@ -399,16 +457,6 @@ __global__ void __launch_bounds__(NT, 1)
     mbar_init(efull, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int t = threadIdx.x; t < k.Tc + k.Tv; t += NT) {
-    const bool vis = t >= k.Tc;
-    const float S = k.sums[t];
-    rsum[vis ? tp.Nc + (t - k.Tc) : t] = S > 0.0f ? 1.0f / S : 0.0f;
-    const int n = vis ? k.nv : k.nc, tt = vis ? t - k.Tc : t;
-    const int i = tt / n, j = tt % n;
-    tab_pos[t] = (uint16_t)((i + 1) * (n + 2) + (j + 1));
-    tab_border[t] = pack_border(i, j, n);
-  }
-  for (int q = threadIdx.x; q < 5; q += NT) flag_mask[q] = 0;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(tmem_holder))
@@ -424,6 +472,14 @@ __global__ void __launch_bounds__(NT, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&map_dist) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&map_rad) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&map_wc) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&map_wv) : "memory");
+      if (kSplitW) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&map_wc_lo) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&map_wv_lo) : "memory");
+      }
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -462,8 +518,7 @@ __global__ void __launch_bounds__(NT, 1)
         ok = mbar_wait(&tempty[b], tph ^ 1, err);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t dv = tmem + b * 256 + tp.col_v;
-        const uint32_t dc = tmem + b * 256 + tp.col_c;
+        const uint32_t dbase = tmem + b * 256;
         for (int kc = 0; kc < tp.nchunks; ++kc) {
           ok = mbar_wait(&conv[s], ph, err);
           if (!ok) break;
@@ -472,21 +527,27 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
           for (int ks = 0; ks < ROWB / 32; ++ks) {     // one MMA K step per 32 bytes of row
             const int kb = ks * 32;
-            const uint64_t av = sdesc<ROWB>(st + kb);
-            const uint64_t ac = sdesc<ROWB>(st + (size_t)(tp.crow + 3 * GRP - 128) * ROWB + kb);
-            const uint64_t bv = sdesc<ROWB>(st + tp.off_wv + kb);
-            const uint64_t bc = sdesc<ROWB>(st + tp.off_wc + kb);
             const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-            mma<FORM>(dv, av, bv, tp.idesc_v, acc);
-            mma<FORM>(dc, ac, bc, tp.idesc_c, acc);
-            if (kSplitW) {
-              mma<FORM>(dv, av, sdesc<ROWB>(st + tp.off_wv_lo + kb), tp.idesc_v, 1u);
-              mma<FORM>(dc, ac, sdesc<ROWB>(st + tp.off_wc_lo + kb), tp.idesc_c, 1u);
+            const uint64_t bx = sdesc<ROWB>(st + kb);                          // d | d^2
+            const uint64_t bl = sdesc<ROWB>(st + 2 * GRP * ROWB + kb);        // d^2 lo
+            const uint64_t bc = sdesc<ROWB>(st + (size_t)tp.crow * ROWB + kb);   // R | G | B
+            for (int j = 0; j < tp.ntv; ++j) {
+              const uint32_t dv = dbase + 64 * j;
+              const uint64_t av = sdesc<ROWB>(st + tp.off_wv + (size_t)j * MT * ROWB + kb);
+              mma<FORM>(dv, av, bx, tp.idesc64, acc);
+              if (!kSplitA) mma<FORM>(dv + GRP, av, bl, tp.idesc32, 1u);
+              if (kSplitW)
+                mma<FORM>(dv, sdesc<ROWB>(st + tp.off_wv_lo + (size_t)j * MT * ROWB + kb), bx, tp.idesc64, 1u);
+              if (kSplitA) mma<FORM>(dv, av, sdesc<ROWB>(st + tp.off_a_lo + kb), tp.idesc64, 1u);
             }
-            if (kSplitA) {
-              uint8_t* lo = st + tp.off_a_lo;
-              mma<FORM>(dv, sdesc<ROWB>(lo + kb), bv, tp.idesc_v, 1u);
-              mma<FORM>(dc, sdesc<ROWB>(lo + (size_t)(tp.crow + 3 * GRP - 128) * ROWB + kb), bc, tp.idesc_c, 1u);
+            for (int j = 0; j < tp.ntc; ++j) {
+              const uint32_t dc = dbase + 64 * tp.ntv + 96 * j;
+              const uint64_t ac = sdesc<ROWB>(st + tp.off_wc + (size_t)j * MT * ROWB + kb);
+              mma<FORM>(dc, ac, bc, tp.idesc96, acc);
+              if (kSplitW)
+                mma<FORM>(dc, sdesc<ROWB>(st + tp.off_wc_lo + (size_t)j * MT * ROWB + kb), bc, tp.idesc96, 1u);
+              if (kSplitA)
+                mma<FORM>(dc, ac, sdesc<ROWB>(st + tp.off_a_lo + (size_t)tp.crow * ROWB + kb), tp.idesc96, 1u);
             }
           }
           mma_commit(&empty[s]);                       // stage free once these MMAs finish
@@ -526,7 +587,7 @@ __global__ void __launch_bounds__(NT, 1)
             *(float4*)(st + (size_t)(GRP * CPR + ct + 64 * u) * 16) =
                 make_float4(d[u].x * d[u].x, d[u].y * d[u].y, d[u].z * d[u].z, d[u].w * d[u].w);
           conv_bar();
-          constexpr int ACH = 160 * CPR / 64;          // chunks per thread over the A tile's 160 rows
+          constexpr int ACH = 160 * CPR / 64;          // chunks per thread over the B tile's 160 rows
           uint4 x[ACH];
 #pragma unroll
           for (int u = 0; u < ACH; ++u) x[u] = *(const uint4*)(st + (size_t)(ct + 64 * u) * 16);
@@ -589,20 +650,40 @@ __global__ void __launch_bounds__(NT, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int e = threadIdx.x - 128;                   // 0..255
-    const int ew = e >> 5;                             // epilogue warp 0..7
+    const int e = threadIdx.x - 128;                   // 0..EPI_THREADS-1
+    const int ew = e >> 5;                             // epilogue warp 0..EPI_WARPS-1
     const int quarter = warp & 3;                      // TMEM lanes 32*quarter .. +32
-    const int half = ew >> 2;                          // which 16-column half of a pass it loads
-    const float h = *k.hy, omh = 1.0f - h;
-    const float d2_scale = FORM == kF16 ? 256.0f : 1.0f;
-    constexpr bool d2_lo = FORM != kF32;               // d^2 lo rows at lanes 64..95
-    const int kind = k.color_code;
-    int b = 0;
-    uint32_t tph = 0, eph = 0;
-    bool ok = true;
+    const int slot = ew >> 2;                          // which of the quarter's three warps
     // thread 0 streams each item's old texels and codes into shared memory as
     // soon as the previous item's tiles have been written back
     if (e == 0 && blockIdx.x < tp.items) prefetch_item(k, np, blockIdx.x * np, sb, st_c, st_v, ls_c, ls_v, efull);
+    // per-texel tables, built while the first stages load
+    for (int t = e; t < k.Tc + k.Tv; t += EPI_THREADS) {
+      const bool vis = t >= k.Tc;
+      const float S = k.sums[t];
+      rsum[t] = S > 0.0f ? 1.0f / S : 0.0f;
+      const int n = vis ? k.nv : k.nc, tt = vis ? t - k.Tc : t;
+      const int i = tt / n, j = tt % n;
+      const int src = (i + 1) * (n + 2) + (j + 1);
+      tab_pos[t] = (uint16_t)src;
+      int tr[8], tc[8];
+      const int nb = pv::border_targets(i, j, n, tr, tc);
+      uint32_t* g = vis ? gb + tp.gb_c : gb;
+      for (int q = 0; q < nb; ++q)
+        g[ring_slot(tr[q], tc[q], n)] = (uint32_t)(tr[q] * (n + 2) + tc[q]) | ((uint32_t)src << 16);
+    }
+    if (e < 4) flag_mask[e] = 0;
+    epi_bar();
+    const float h = *k.hy, omh = 1.0f - h;
+    const float d2_scale = FORM == kF16 ? 256.0f : 1.0f;
+    const int kind = k.color_code;
+    const bool f16 = k.state_fmt == PV_FMT_F16;
+    const uint32_t s_st_c = smem_u32(st_c), s_st_v = smem_u32(st_v);
+    const uint32_t s_ls_c = smem_u32(ls_c), s_ls_v = smem_u32(ls_v);
+    const uint32_t s_rsum = smem_u32(rsum), s_pos = smem_u32(tab_pos), s_gb = smem_u32(gb);
+    int b = 0, par = 0;
+    uint32_t tph = 0, eph = 0;
+    bool ok = true;
     for (int item = blockIdx.x; item < tp.items && ok; item += gridDim.x) {
       const int p0 = item * np;
       const int npi = min(np, k.P - p0);
@@ -611,52 +692,28 @@ __global__ void __launch_bounds__(NT, 1)
       if (!ok) break;
       eph ^= 1;
       tc_fence_after();
-      const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + b * 256;
-      const int npass_c = (k.Tc + 31) / 32, npass_v = (k.Tv + 31) / 32;
-      for (int pass = 0; pass < npass_c + npass_v; ++pass) {
-        const bool vis = pass >= npass_c;
-        const int blk = vis ? pass - npass_c : pass;
-        const int N = vis ? tp.Nv : tp.Nc;
-        const int c16 = 32 * blk + 16 * half;          // first of the 16 columns this warp loads
-        if (c16 < N) {
-          float v[16];
-          tmem_ld16(trow + (vis ? tp.col_v : tp.col_c) + c16, v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) ms[(16 * half + j) * MS_LD + quarter * 32 + lane] = v[j];
-        }
-        epi_bar();
-        // lane <-> texel t of this pass; constants of that texel
-        const int T = vis ? k.Tv : k.Tc;
-        const int t = 32 * blk + lane;
-        LaneTexel lt;
-        lt.has = t < T;
-        const int tg = lt.has ? (vis ? k.Tc + t : t) : 0;
-        const uint64_t bord = tab_border[tg];
-        lt.pos = tab_pos[tg];
-        lt.nb = lt.has ? (int)(bord >> 48) : 0;
-        lt.b0 = (uint32_t)(bord & 0xFFFFu);
-        lt.b1 = (uint32_t)((bord >> 16) & 0xFFFFu);
-        lt.b2 = (uint32_t)((bord >> 32) & 0xFFFFu);
-        lt.rS = lt.has ? rsum[(vis ? tp.Nc : 0) + t] : 0.0f;
-        lt.t = lt.has ? t : 0;
-        const float* mcol = ms + lane * MS_LD;
-        void* tiles = vis ? (void*)st_v : (void*)st_c;
-        const int tile_elems = vis ? k.sv_stride : k.sc_stride;
-        const uint16_t* codes = vis ? ls_v : ls_c;
-        const int code_elems = vis ? k.lv_stride : k.lc_stride;
-        const bool f16 = k.state_fmt == PV_FMT_F16;
-        if (vis) {
-          if (f16) epi_pass<0, 0, true, d2_lo>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, d2_scale, ew, lane, flag_mask);
-          else epi_pass<1, 0, true, d2_lo>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, d2_scale, ew, lane, flag_mask);
-        } else if (kind == PV_CODE_UNORM10) {
-          if (f16) epi_pass<0, PV_CODE_UNORM10, false, false>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_mask);
-          else epi_pass<1, PV_CODE_UNORM10, false, false>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_mask);
-        } else {
-          if (f16) epi_pass<0, PV_CODE_UF10, false, false>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_mask);
-          else epi_pass<1, PV_CODE_UF10, false, false>(lt, mcol, npi, np, tiles, tile_elems, codes, code_elems, h, omh, 1.0f, ew, lane, flag_mask);
-        }
-        epi_bar();
+      const uint32_t tcol = tmem + ((uint32_t)(quarter * 32) << 16) + b * 256;
+      const uint32_t tcol_c = tcol + 64 * tp.ntv;
+      int task = 0;
+      uint32_t mv, mc;
+      if (f16) {
+        mv = epi_texture<0, 0, true>(tcol, tp.ntv, k.Tv, quarter, slot, lane, task, s_rsum + 4u * k.Tc, s_pos + 2u * k.Tc,
+                                     s_st_v, k.sv_stride, s_ls_v, k.lv_stride, np, npi, h, omh, d2_scale);
+        if (kind == PV_CODE_UNORM10)
+          mc = epi_texture<0, PV_CODE_UNORM10, false>(tcol_c, tp.ntc, k.Tc, quarter, slot, lane, task, s_rsum, s_pos,
+                                                      s_st_c, k.sc_stride, s_ls_c, k.lc_stride, np, npi, h, omh, 1.0f);
+        else
+          mc = epi_texture<0, PV_CODE_UF10, false>(tcol_c, tp.ntc, k.Tc, quarter, slot, lane, task, s_rsum, s_pos,
+                                                   s_st_c, k.sc_stride, s_ls_c, k.lc_stride, np, npi, h, omh, 1.0f);
+      } else {
+        mv = epi_texture<1, 0, true>(tcol, tp.ntv, k.Tv, quarter, slot, lane, task, s_rsum + 4u * k.Tc, s_pos + 2u * k.Tc,
+                                     s_st_v, k.sv_stride, s_ls_v, k.lv_stride, np, npi, h, omh, d2_scale);
+        if (kind == PV_CODE_UNORM10)
+          mc = epi_texture<1, PV_CODE_UNORM10, false>(tcol_c, tp.ntc, k.Tc, quarter, slot, lane, task, s_rsum, s_pos,
+                                                      s_st_c, k.sc_stride, s_ls_c, k.lc_stride, np, npi, h, omh, 1.0f);
+        else
+          mc = epi_texture<1, PV_CODE_UF10, false>(tcol_c, tp.ntc, k.Tc, quarter, slot, lane, task, s_rsum, s_pos,
+                                                   s_st_c, k.sc_stride, s_ls_c, k.lc_stride, np, npi, h, omh, 1.0f);
       }
       // accumulators consumed: hand the TMEM buffer back to the MMA thread
       tc_fence_before();
@@ -665,15 +722,30 @@ __global__ void __launch_bounds__(NT, 1)
         b = 0;
         tph ^= 1;
       }
+      mc = __reduce_or_sync(0xffffffffu, mc);
+      mv = __reduce_or_sync(0xffffffffu, mv);
+      uint32_t* fm = flag_mask + 2 * par;
+      if (lane == 0) {
+        if (mc) atomicOr(&fm[0], mc);
+        if (mv) atomicOr(&fm[1], mv);
+      }
+      epi_bar();                                       // interior texels and flags of the item done
       if (e < 2) {                                     // changed-probe bits of this item
-        const uint32_t m = e == 0 ? (flag_mask[0] | flag_mask[1] | flag_mask[2]) : (flag_mask[3] | flag_mask[4]);
+        const uint32_t m = fm[e];
+        fm[e] = 0;                                     // this parity's masks are next used two items on
         const int sh = p0 & 31;
         uint32_t* w = &k.chg[e * k.chg_words + (p0 >> 5)];
         if (m << sh) atomicOr(w, m << sh);
         if (sh && (m >> (32 - sh))) atomicOr(w + 1, m >> (32 - sh));
       }
-      epi_bar();
-      if (e < 5) flag_mask[e] = 0;
+      par ^= 1;
+      if (f16) {
+        guard_band<0>(s_st_c, s_gb, tp.gb_c, 3, k.sc_stride, np, npi, ew, lane);
+        guard_band<0>(s_st_v, s_gb + 4u * tp.gb_c, tp.gb_v, 2, k.sv_stride, np, npi, ew, lane);
+      } else {
+        guard_band<1>(s_st_c, s_gb, tp.gb_c, 3, k.sc_stride, np, npi, ew, lane);
+        guard_band<1>(s_st_v, s_gb + 4u * tp.gb_c, tp.gb_v, 2, k.sv_stride, np, npi, ew, lane);
+      }
       fence_proxy_async();
       epi_bar();
       if (e == 0) {
@@ -755,7 +827,6 @@ size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 bool pv_tc_supported(const pv_desc* d, const char** why) {
   const int ob = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
   const int nc = d->color_interior, nv = d->vis_interior;
-  const int Nc = ((nc * nc + 15) / 16) * 16, Nv = ((nv * nv + 15) / 16) * 16;
   if (nc < 2 || nv < 2) {
     if (why) *why = "tile interiors below 2x2 (guard-band table holds three copies per texel)";
     return false;
@@ -764,7 +835,7 @@ bool pv_tc_supported(const pv_desc* d, const char** why) {
     if (why) *why = "rays_per_probe * operand bytes must be a multiple of 16 (TMA row pitch)";
     return false;
   }
-  if (Nc + Nv > 512 || Nv > 256 || Nc > 256) {
+  if (nc * nc > 2 * MT || nv * nv > 2 * MT) {
     if (why) *why = "tile interiors too large for the tensor-memory accumulators";
     return false;
   }
@@ -797,82 +868,106 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int sb = v->state_bytes;
   const int np_max = sb == 2 ? 32 : 16;
-  int np = (k.P + sms - 1) / sms;
-  np = np < 1 ? 1 : (np > np_max ? np_max : np);
-  tp.np = np;
-  tp.items = (k.P + np - 1) / np;
-  pl->grid = tp.items < sms ? tp.items : sms;
   const int ROWB = form == kF32 ? row_bytes<kF32>() : row_bytes<kF16>();
   tp.kc = ROWB / ob;
   tp.nchunks = (k.R + tp.kc - 1) / tp.kc;
-  tp.Nc = k.tc_pad;
-  tp.Nv = k.tv_pad;
-  tp.nbuf = tp.Nc + tp.Nv <= 256 ? 2 : 1;
-  tp.col_v = 0;
-  tp.col_c = tp.Nv;
+  tp.ntc = (k.Tc + MT - 1) / MT;
+  tp.ntv = (k.Tv + MT - 1) / MT;
+  tp.bufcols = 64 * tp.ntv + 96 * tp.ntc;
+  tp.nbuf = tp.bufcols <= 256 ? 2 : 1;         // buffers at TMEM columns 0 and 256
   tp.a_rows = form == kF32 ? 160 : 192;
   tp.crow = form == kF32 ? 64 : 96;
-  // stage layout
+  tp.gb_c = 4 * k.nc + 4;
+  tp.gb_v = 4 * k.nv + 4;
+  // stage layout: ray tile, its TF32 low parts, then the weight planes. A
+  // weight plane holds only the texture's rows (tc_pad / tv_pad of them), but
+  // its MMAs read whole 128-row tiles: the rows past the plane read whatever
+  // follows (the lanes they produce are ignored); `guard` keeps those reads
+  // of the last stage inside the allocation.
   size_t off = 0;
   const size_t a_b = align1k((size_t)tp.a_rows * ROWB);
   off += a_b;
   tp.off_a_lo = (int)off;
   if (form == kF32) off += a_b;
-  tp.off_wc = (int)off;
-  off += align1k((size_t)tp.Nc * ROWB);
-  tp.off_wv = (int)off;
-  off += align1k((size_t)tp.Nv * ROWB);
-  tp.off_wc_lo = (int)off;
-  if (form != kF16) off += align1k((size_t)tp.Nc * ROWB);
-  tp.off_wv_lo = (int)off;
-  if (form != kF16) off += align1k((size_t)tp.Nv * ROWB);
+  size_t ext = 0;
+  auto plane = [&](int rows, int ntiles) {
+    const size_t o = off;
+    off += align1k((size_t)rows * ROWB);
+    const size_t end = o + (size_t)ntiles * MT * ROWB;
+    ext = end > ext ? end : ext;
+    return (int)o;
+  };
+  tp.off_wc = plane(k.tc_pad, tp.ntc);
+  tp.off_wv = plane(k.tv_pad, tp.ntv);
+  tp.off_wc_lo = tp.off_wc;
+  tp.off_wv_lo = tp.off_wv;
+  if (form != kF16) {
+    tp.off_wc_lo = plane(k.tc_pad, tp.ntc);
+    tp.off_wv_lo = plane(k.tv_pad, tp.ntv);
+  }
   tp.stage_bytes = (int)off;
-  tp.stage_tx = (uint32_t)((4 * np + (form != kF16 ? 2 : 1) * (tp.Nc + tp.Nv)) * ROWB);
-  // epilogue region
-  const size_t epi_state = (size_t)np * (3 * k.sc_stride + 2 * k.sv_stride) * sb;
-  const size_t epi_last = (size_t)np * (3 * k.lc_stride + 2 * k.lv_stride) * 2;
-  const size_t tab = (size_t)(k.Tc + k.Tv) * 10;
-  const size_t epi = align1k(epi_state) + align1k(epi_last) + align1k((size_t)32 * MS_LD * 4) +
-                     align1k((size_t)(tp.Nc + tp.Nv) * 4) + align1k(5 * GRP * 4) + align1k(tab) + 1024;
-  const size_t budget = (size_t)smem_max - 1024 - epi;
-  int stages = (int)(budget / tp.stage_bytes);
-  if (stages > 4) stages = 4;
+  const size_t guard = ext > off ? align1k(ext - off) : 0;
+  // probes per work item: one item per SM where possible, fewer probes when
+  // the item's tiles would leave room for less than two stages
+  const size_t n_rsum = (size_t)(k.Tc + k.Tv) * 4, n_pos = (size_t)(k.Tc + k.Tv) * 2;
+  const size_t n_gb = (size_t)(tp.gb_c + tp.gb_v) * 4;
+  int np = (k.P + sms - 1) / sms;
+  np = np < 1 ? 1 : (np > np_max ? np_max : np);
+  int stages = 0;
+  size_t epi_state = 0, epi_last = 0;
+  for (; np >= 1; --np) {
+    // the epilogue's last row group of a channel reads up to 7 rows past the
+    // item, so each region ends with 8 spare rows
+    epi_state = ((size_t)np * (3 * k.sc_stride + 2 * k.sv_stride) + 8 * (size_t)k.sv_stride) * sb;
+    epi_last = ((size_t)np * (3 * k.lc_stride + 2 * k.lv_stride) + 8 * (size_t)k.lv_stride) * 2;
+    const size_t epi = align1k(epi_state) + align1k(epi_last) + align1k(n_rsum) + align1k(n_pos) +
+                       align1k(n_gb) + 1024 + 1024;
+    const size_t need = 1024 + epi + guard;
+    stages = need < (size_t)smem_max ? (int)(((size_t)smem_max - need) / tp.stage_bytes) : 0;
+    if (stages >= 2) break;
+  }
   if (stages < 2) {
     delete pl;
     return cudaErrorInvalidConfiguration;
   }
+  if (stages > 4) stages = 4;
+  tp.np = np;
+  tp.items = (k.P + np - 1) / np;
+  pl->grid = tp.items < sms ? tp.items : sms;
   tp.stages = stages;
-  off = (size_t)stages * tp.stage_bytes;
+  tp.stage_tx = (uint32_t)((4 * np + (form != kF16 ? 2 : 1) * (k.tc_pad + k.tv_pad)) * ROWB);
+  off = (size_t)stages * tp.stage_bytes + guard;
   tp.off_state = (int)off;
   off += align1k(epi_state);
   tp.off_last = (int)off;
   off += align1k(epi_last);
-  tp.off_ms = (int)off;
-  off += align1k((size_t)32 * MS_LD * 4);
-  tp.off_invs = (int)off;
-  off += align1k((size_t)(tp.Nc + tp.Nv) * 4);
+  tp.off_rsum = (int)off;
+  off += align1k(n_rsum);
+  tp.off_pos = (int)off;
+  off += align1k(n_pos);
+  tp.off_gb = (int)off;
+  off += align1k(n_gb);
   tp.off_flags = (int)off;
-  off += align1k(5 * GRP * 4);
-  tp.off_tab = (int)off;
-  off += align1k(tab);
+  off += 1024;
   tp.off_bar = (int)off;
   off += 1024;
   pl->smem = off + 1024;                       // slack for aligning the dynamic base
-  tp.idesc_c = make_idesc(form, 128, tp.Nc);
-  tp.idesc_v = make_idesc(form, 128, tp.Nv);
+  tp.idesc32 = make_idesc(form, MT, 32);
+  tp.idesc64 = make_idesc(form, MT, 64);
+  tp.idesc96 = make_idesc(form, MT, 96);
   // weight tensor maps (fixed for the volume's life)
-  const size_t plane = (size_t)(k.tc_pad + k.tv_pad) * k.r_pad;
+  const size_t wplane = (size_t)(k.tc_pad + k.tv_pad) * k.r_pad;
   const uint8_t* w = (const uint8_t*)k.w_op;
-  e = encode_2d(&pl->wc, k.operand_fmt, w, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.Nc);
+  e = encode_2d(&pl->wc, k.operand_fmt, w, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc, k.tc_pad);
   if (e == cudaSuccess)
     e = encode_2d(&pl->wv, k.operand_fmt, w + (size_t)k.tc_pad * k.r_pad * ob, k.r_pad, k.tv_pad,
-                  (uint64_t)k.r_pad * ob, tp.kc, tp.Nv);
+                  (uint64_t)k.r_pad * ob, tp.kc, k.tv_pad);
   if (e == cudaSuccess && form != kF16) {
-    e = encode_2d(&pl->wc_lo, k.operand_fmt, w + plane * ob, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob,
-                  tp.kc, tp.Nc);
+    e = encode_2d(&pl->wc_lo, k.operand_fmt, w + wplane * ob, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob,
+                  tp.kc, k.tc_pad);
     if (e == cudaSuccess)
-      e = encode_2d(&pl->wv_lo, k.operand_fmt, w + (plane + (size_t)k.tc_pad * k.r_pad) * ob, k.r_pad,
-                    k.tv_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.Nv);
+      e = encode_2d(&pl->wv_lo, k.operand_fmt, w + (wplane + (size_t)k.tc_pad * k.r_pad) * ob, k.r_pad,
+                    k.tv_pad, (uint64_t)k.r_pad * ob, tp.kc, k.tv_pad);
   } else {
     pl->wc_lo = pl->wc;
     pl->wv_lo = pl->wv;

@@ -17,56 +17,51 @@
 
 namespace pv {
 
-// Drop `s` low bits of x with round-to-nearest-even (0 < s < 32).
-__device__ __forceinline__ uint32_t rne_shift(uint32_t x, uint32_t s) {
-  uint32_t q = x >> s;
-  uint32_t rem = x & ((1u << s) - 1u);
-  uint32_t half = 1u << (s - 1);
-  return q + ((rem > half) || (rem == half && (q & 1u)));
+// Round-to-nearest-even of x / 2^s (0 < s < 32) without a branch; exact as
+// long as x + 2^(s-1) fits in 32 bits.
+__device__ __forceinline__ uint32_t rne_shift_fast(uint32_t x, uint32_t s) {
+  return (x + ((1u << (s - 1)) - 1u) + ((x >> s) & 1u)) >> s;
 }
 
-// UF10 code of a binary16 value given by its bits.
+// UF10 code of a binary16 value given by its bits. Branch-free: the code is
+// the magnitude bits with 5 mantissa bits rounded off (binary16 and UF10
+// share exponent bias and range, subnormals included); +inf rounds to 0x3E0
+// and clamps with the finite overflow to 0x3DF. Bits above 0x7C00 are a set
+// sign or a NaN, which give 0.
 __device__ __forceinline__ uint32_t uf10_from_half_bits(uint32_t h) {
-  if (h & 0x8000u) return 0u;                         // negative, -0, negative NaN
-  uint32_t e = (h >> 10) & 0x1Fu, m = h & 0x3FFu;
-  if (e == 31u) return m ? 0u : 0x3DFu;               // NaN -> 0, +inf -> top code
-  // binary16 and UF10 share exponent bias and range, so the code is the
-  // magnitude bits with 5 mantissa bits rounded off (subnormals included).
-  uint32_t c = rne_shift(h & 0x7FFFu, 5);
-  return c > 0x3DFu ? 0x3DFu : c;
+  const uint32_t a = h & 0x7FFFu;
+  const uint32_t c = min(rne_shift_fast(a, 5), 0x3DFu);
+  return h <= 0x7C00u ? c : 0u;
 }
 
-// UF10 code of a binary32 value given by its bits (one direct rounding).
+// UF10 code of a binary32 value given by its bits (one direct rounding),
+// evaluated for both the UF10 normal and subnormal ranges and selected.
 __device__ __forceinline__ uint32_t uf10_from_float_bits(uint32_t f) {
-  if (f & 0x80000000u) return 0u;
-  uint32_t e = (f >> 23) & 0xFFu, m = f & 0x7FFFFFu;
-  if (e == 255u) return m ? 0u : 0x3DFu;
-  if (e >= 113u) {                                    // UF10 normal range (exponent >= -14)
-    uint32_t mag = ((e - 112u) << 23) | m;
-    uint32_t c = rne_shift(mag, 18);
-    return c > 0x3DFu ? 0x3DFu : c;
-  }
-  if (e == 0u) return 0u;                             // binary32 subnormal: far below 2^-20
+  const uint32_t e = (f >> 23) & 0xFFu, m = f & 0x7FFFFFu;
+  // UF10 normal range (exponent >= -14): rebias the exponent to 15
+  const uint32_t mag = ((e - 112u) << 23) | m;
+  uint32_t cn = rne_shift_fast(mag, 18);
+  cn = cn > 0x3DFu ? 0x3DFu : cn;
   // UF10 subnormal: code = round(value / 2^-19), value = (2^23 + m) * 2^(e-150)
-  uint32_t s = 131u - e;                              // >= 19
-  if (s > 31u) return 0u;
-  return rne_shift(0x800000u | m, s);
+  const uint32_t sh = 131u - e;                       // 19..31 for e in 100..112
+  const uint32_t cs = (e >= 100u && e <= 112u) ? rne_shift_fast(0x800000u | m, sh < 31u ? sh : 31u) : 0u;
+  uint32_t c = e >= 113u ? cn : cs;                   // e < 100 (incl. subnormal binary32): 0
+  c = e == 255u ? (m ? 0u : 0x3DFu) : c;
+  return (f & 0x80000000u) ? 0u : c;
 }
 
-// round(clamp(x,0,1)*1023) with ties to even, exact for any float x.
+// round(clamp(x,0,1)*1023) with ties to even, exact for any float x: the
+// product's rounding residual decides values that round to a tie. NaN clamps
+// to 0 (fmaxf returns the non-NaN operand).
 __device__ __forceinline__ uint32_t unorm10_from_float(float x) {
-  if (!(x > 0.0f)) return 0u;                         // also NaN
-  if (x >= 1.0f) return 1023u;
-  float p = x * 1023.0f;
-  float e = fmaf(x, 1023.0f, -p);                     // exact residual of the product
-  float fl = floorf(p);
-  float fr = p - fl;                                  // exact
-  uint32_t k = (uint32_t)fl;
-  if (fr > 0.5f) return k + 1u;
-  if (fr < 0.5f) return k;
-  if (e > 0.0f) return k + 1u;                        // true value above the tie
-  if (e < 0.0f) return k;
-  return k + (k & 1u);                                // exact tie: to even
+  const float xc = fminf(fmaxf(x, 0.0f), 1.0f);
+  const float p = xc * 1023.0f;
+  const float e = fmaf(xc, 1023.0f, -p);              // exact residual of the product
+  const float fl = floorf(p);
+  const float fr = p - fl;                            // exact
+  const uint32_t k = (uint32_t)fl;
+  const bool up = fr > 0.5f || (fr == 0.5f && (e > 0.0f || (e == 0.0f && (k & 1u))));
+  return k + (up ? 1u : 0u);
 }
 
 __device__ __forceinline__ float load_state(const void* base, size_t i, int fmt) {
