@@ -4,20 +4,22 @@
 // The blend is a dense contraction because every probe of a volume shares the
 // frame's ray directions: per texel t and probe row x (a colour channel, d or
 // d^2), acc[t, x] = sum_r W[t, r] x[r]. Texels form the MMA's M dimension (one
-// tensor-memory lane per texel, 128-texel tiles), the probe rows of a work
-// item (np <= 32 probes per row group) its N dimension, rays its K dimension:
+// tensor-memory lane per texel), the probe rows of a work item (np <= 32
+// probes per row group) its N dimension, rays its K dimension:
 //
-//   A (shared memory, K-major): the weight tiles W_c [Tc x K] and W_v [Tv x K]
-//     from the weights kernel. Rows past the texture's texels are never
-//     loaded; the lanes they produce are ignored.
+//   A (shared memory, K-major): the weights from the weights kernel, one
+//     combined texel list in 128-row tiles: visibility texels in rows
+//     0..Tv-1, colour texels from the next multiple of 8. Rows past the
+//     texels are never loaded; the lanes they produce are ignored.
 //   B (shared memory, K-major, one row per probe row, row groups of 32):
 //     [ d | d^2 (hi) | d^2 lo (16-bit forms) | R | G | B ]
 //     d and the colour planes come straight from HBM by TMA; d^2 is formed on
 //     chip by two converter warps (its rounding to the operand format is split
 //     into hi + lo parts so that it costs no accuracy).
-//   D (tensor memory, FP32), per 128-texel tile: visibility N = 64 columns
-//     (d, d^2; the d^2 lo rows accumulate into the d^2 columns with N = 32),
-//     colour N = 96 columns (R, G, B).
+//   D (tensor memory, FP32): one MMA per tile and K step, with the B rows its
+//     texels need: the visibility rows, the colour rows, or all of B for the
+//     tile that holds both. An MMA with M = 128 costs the same up to N = 112,
+//     so a few wide MMAs beat many narrow ones.
 //
 // Operand forms (pv_desc.operand_fmt):
 //   F16  kind::f16, binary16 inputs; visibility weights scaled by 2^15 and
@@ -53,6 +55,7 @@
 #include <cuda_fp16.h>
 #include <stdio.h>
 #include <type_traits>
+#include <stdlib.h>
 #include <string.h>
 
 #include "pv_codes.cuh"
@@ -72,19 +75,28 @@ template <int FORM>
 __host__ __device__ constexpr int row_bytes() { return FORM == 2 ? 32 : 64; }
 constexpr int GRP = 32;                  // probe rows per row group of the B tile
 constexpr int MT = 128;                  // texels per MMA tile (M)
+enum TileKind { kTileVis = 0, kTileCol = 1, kTileBoth = 2 };
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+// binary16 operand form: d^2 enters the MMA scaled by 2^-4 (exact), which
+// keeps the high part of d^2 for hit distances up to 2^10 in binary16 range
+constexpr float kD2ScaleF16 = 0.0625f;
 
 struct TcParams {
   pv_dev k;
-  int np, items, stages, kc, nchunks;
-  int ntc, ntv, bufcols, nbuf;           // 128-texel tiles per texture; TMEM columns a buffer uses
+  int np, items, iters, stages, kc, nchunks;
+  int cluster;                           // CTAs per cluster sharing each weight chunk
+  int ntiles, bufcols, nbuf;             // 128-row texel tiles; TMEM columns a buffer uses
+  int vb;                                // tile row of colour texel 0 (visibility texels: rows 0..Tv-1)
+  int vbox, cbox;                        // weight rows loaded per chunk: visibility, colour
+  int nvc;                               // B rows (and TMEM columns) of the visibility block
   int crow;                              // first B row of the colour block
   int a_rows;                            // rows of the ray (B) tile
-  int off_a_lo, off_wc, off_wc_lo, off_wv, off_wv_lo, stage_bytes;
+  int tkind[4], tbase[4];                // per tile: which B rows (kTileVis/Col/Both); first TMEM column
+  uint32_t tidesc[4];
+  int off_a_lo, off_w, off_w_lo, stage_bytes;
   int off_state, off_last, off_rsum, off_pos, off_gb, off_flags, off_bar;
   int gb_c, gb_v;                        // guard-band texels per tile: 4n + 4
-  uint32_t stage_tx;
-  uint32_t idesc32, idesc64, idesc96;
+  uint32_t stage_tx, w_tx;               // bytes per stage: all, weight tiles only
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -145,6 +157,24 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// The same tile into the same offset of every CTA in `mask` (cluster ranks),
+// each CTA's barrier at `bar`'s offset receiving its bytes.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -181,6 +211,15 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
   }
+}
+// Arrive on the barrier at `bar`'s offset in every CTA of `mask` once this
+// thread's MMAs so far have finished.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -257,18 +296,19 @@ __device__ __forceinline__ uint32_t texel_code(uint32_t b) {
   return SF == 0 ? pv::uf10_from_half_bits(b) : pv::uf10_from_float_bits(b);
 }
 
-// One epilogue task: the 32 accumulator columns at taddr are probe rows
-// p = 0..31 of one channel, and this lane's TMEM lane is one texel, whose
+// One epilogue task: the 32 accumulator columns at taddr (plus those at
+// taddr_lo for an operand split into two parts) are probe rows p = 0..31 of
+// one channel, and this lane's TMEM lane is one texel, whose
 // stored value in row p sits at s_tile + p * row_b and whose last-transmitted
 // code at s_code + p * code_b (shared addresses). Rows go in groups of U: one
 // TMEM load per group, then the group's old texels and last codes, then the
 // arithmetic and stores. The group loop stays rolled so that the epilogue's
 // code is small enough to stay in the instruction cache. Returns the rows
 // whose transmitted code changed as a bit mask (bit p).
-template <int SF, int KIND, bool VIS>
-__device__ __forceinline__ uint32_t epi_task(uint32_t taddr, bool has, uint32_t s_tile, uint32_t s_code, float rS,
-                                             float h, float omh, float scale, uint32_t row_b, uint32_t code_b,
-                                             int npi) {
+template <int SF, int KIND, bool VIS, bool LO>
+__device__ __forceinline__ uint32_t epi_task(uint32_t taddr, uint32_t taddr_lo, bool has, uint32_t s_tile,
+                                             uint32_t s_code, float rS, float h, float omh, float scale,
+                                             uint32_t row_b, uint32_t code_b, int npi) {
   constexpr int SB = StateOps<SF>::SB;
   constexpr int U = 8;
   const float c = omh * (rS * scale);
@@ -284,6 +324,12 @@ __device__ __forceinline__ uint32_t epi_task(uint32_t taddr, bool has, uint32_t 
   for (int g = 0; g < npi; g += U) {
     float v[U];
     tmem_ld8(taddr + (uint32_t)g, v);
+    if (LO) {                                          // accumulator of the operand's low part
+      float w[U];
+      tmem_ld8(taddr_lo + (uint32_t)g, w);
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] += w[u];
+    }
     const uint32_t tb = s_tile + (uint32_t)g * row_b, cb = s_code + (uint32_t)g * code_b;
     // rows of this group inside the item (none for lanes without a texel);
     // rows past the item still load (the shared regions are padded for it)
@@ -309,39 +355,71 @@ __device__ __forceinline__ uint32_t epi_task(uint32_t taddr, bool has, uint32_t 
   return m;
 }
 
-// All tasks of one texture in one TMEM buffer for this warp: tiles j of 128
-// texels, this warp's lane quarter, channels ch; the tasks of a quarter are
-// dealt round-robin to its three warps.
-template <int SF, int KIND, bool VIS>
-__device__ __forceinline__ uint32_t epi_texture(uint32_t tcol, int ntiles, int T, int quarter, int slot, int lane,
-                                                int& task, uint32_t s_rsum, uint32_t s_pos,
-                                                uint32_t s_tiles, int tile_elems, uint32_t s_codes, int code_elems,
-                                                int np, int npi, float h, float omh, float d2_scale) {
+// Shared-memory addresses and sizes the epilogue tasks of an item use.
+struct EpiCtx {
+  uint32_t s_rsum, s_pos;                // per-texel tables: colour texels first, then visibility
+  uint32_t s_st_c, s_st_v, s_ls_c, s_ls_v;
+  int sc_stride, sv_stride, lc_stride, lv_stride;
+  int Tc, Tv, np, npi;
+  float h, omh, d2_scale;
+};
+
+// Tasks of a group of 32 texels of one texture for this warp: the channels
+// (32 TMEM columns each from `col`) dealt round-robin to the three warps of
+// the lane quarter. `t0` is the texture's texel index of lane 0 (lanes
+// outside 0..T-1 have no texel).
+template <int SF, int KIND, bool VIS, bool D2LO>
+__device__ __forceinline__ uint32_t epi_group(const EpiCtx& x, uint32_t col, int t0, int lane, int slot,
+                                              int& task) {
   constexpr int NCH = VIS ? 2 : 3;
-  constexpr int CW = VIS ? 64 : 96;                  // TMEM columns per tile
   constexpr int SB = StateOps<SF>::SB;
+  const int T = VIS ? x.Tv : x.Tc;
+  const int t = t0 + lane;
+  const bool has = t >= 0 && t < T;
+  const int tt = has ? t : (t0 < 0 ? 0 : t0);      // a valid texel for the loads of idle lanes
+  const uint32_t ti = (uint32_t)(VIS ? x.Tc + tt : tt);
+  const float rS = has ? __uint_as_float(lds<4>(x.s_rsum + 4u * ti)) : 0.0f;
+  const uint32_t pos = lds<2>(x.s_pos + 2u * ti);
+  const int tile_elems = VIS ? x.sv_stride : x.sc_stride, code_elems = VIS ? x.lv_stride : x.lc_stride;
   const uint32_t row_b = (uint32_t)tile_elems * SB, code_b = (uint32_t)code_elems * 2;
+  const uint32_t s_tiles = VIS ? x.s_st_v : x.s_st_c, s_codes = VIS ? x.s_ls_v : x.s_ls_c;
   uint32_t m = 0;
-  for (int j = 0; j < ntiles; ++j) {
-    const int t0 = MT * j + GRP * quarter;
-    if (t0 >= T) continue;
-    const int t = t0 + lane;
-    const bool has = t < T;
-    const int tt = has ? t : t0;
-    const float rS = has ? __uint_as_float(lds<4>(s_rsum + 4u * tt)) : 0.0f;
-    const uint32_t pos = lds<2>(s_pos + 2u * tt);
 #pragma unroll 1
-    for (int ch = 0; ch < NCH; ++ch) {
-      const int mine = task++ % 3;
-      if (mine != slot) continue;
-      const float scale = (VIS && ch == 1) ? d2_scale : 1.0f;
-      m |= epi_task<SF, KIND, VIS>(tcol + CW * j + GRP * ch, has,
-                                   s_tiles + (uint32_t)(ch * np) * row_b + pos * SB,
-                                   s_codes + (uint32_t)(ch * np) * code_b + (uint32_t)tt * 2, rS, h, omh, scale,
-                                   row_b, code_b, npi);
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int mine = task++ % 3;
+    if (mine != slot) continue;
+    const uint32_t st = s_tiles + (uint32_t)(ch * x.np) * row_b + pos * SB;
+    const uint32_t sc = s_codes + (uint32_t)(ch * x.np) * code_b + (uint32_t)tt * 2;
+    const uint32_t c = col + GRP * ch;
+    if (VIS && ch == 1) {
+      if (D2LO) m |= epi_task<SF, KIND, VIS, true>(c, c + GRP, has, st, sc, rS, x.h, x.omh, x.d2_scale, row_b, code_b, x.npi);
+      else m |= epi_task<SF, KIND, VIS, false>(c, 0, has, st, sc, rS, x.h, x.omh, x.d2_scale, row_b, code_b, x.npi);
+    } else {
+      m |= epi_task<SF, KIND, VIS, false>(c, 0, has, st, sc, rS, x.h, x.omh, 1.0f, row_b, code_b, x.npi);
     }
   }
   return m;
+}
+
+// All tasks of one item in one TMEM buffer (lane quarter of this warp, TMEM
+// address `tq` of column 0): per 128-row tile, the visibility texels and the
+// colour texels that fall into this quarter. Returns the changed-probe masks
+// (colour, visibility).
+template <int SF, int KIND, bool D2LO>
+__device__ __forceinline__ void epi_item(const TcParams& tp, const EpiCtx& x, uint32_t tq, int quarter, int lane,
+                                         int slot, uint32_t& mc, uint32_t& mv) {
+  int task = 0;
+  mc = 0;
+  mv = 0;
+  for (int j = 0; j < tp.ntiles; ++j) {
+    const int r0 = MT * j + GRP * quarter;             // tile row of lane 0
+    const uint32_t col = tq + (uint32_t)tp.tbase[j];
+    if (tp.tkind[j] != kTileCol && r0 < x.Tv) mv |= epi_group<SF, 0, true, D2LO>(x, col, r0, lane, slot, task);
+    const int c0 = r0 - tp.vb;                         // colour texel of lane 0
+    if (tp.tkind[j] != kTileVis && c0 + GRP > 0 && c0 < x.Tc)
+      mc |= epi_group<SF, KIND, false, false>(x, col + (tp.tkind[j] == kTileBoth ? (uint32_t)tp.crow : 0u), c0,
+                                             lane, slot, task);
+  }
 }
 
 // The item's old texels and last-transmitted codes, into shared memory.
@@ -448,7 +526,7 @@ __global__ void __launch_bounds__(NT, 1)
     for (int s = 0; s < tp.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], 64);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], tp.cluster);          // every CTA of the cluster frees the stage
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -464,10 +542,13 @@ __global__ void __launch_bounds__(NT, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  __syncthreads();
+  if (tp.cluster > 1) cluster_sync();               // peers' barriers exist before any multicast
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   int* err = k.err;
+  const uint32_t crank = tp.cluster > 1 ? cluster_rank() : 0u;
+  const uint16_t cmask = (uint16_t)((1u << tp.cluster) - 1u);
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -483,28 +564,59 @@ __global__ void __launch_bounds__(NT, 1)
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < tp.items && ok; item += gridDim.x) {
+      // Every CTA of a cluster runs the same number of rounds (a CTA past the
+      // last item runs a round without rays, so that the weight chunks it
+      // multicasts and the stages it frees keep its peers going). Chunk kc's
+      // weight tiles are loaded once per cluster, by rank kc % cluster, into
+      // every CTA's stage.
+      for (int it = 0; it < tp.iters && ok; ++it) {
+        const int item = blockIdx.x + it * gridDim.x;
+        const bool real = item < tp.items;
         const int p0 = item * np;
-        // ray and weight tiles, chunk by chunk
         for (int kc = 0; kc < tp.nchunks; ++kc) {
           ok = mbar_wait(&empty[s], ph ^ 1, err);
           if (!ok) break;
           uint8_t* st = smem + (size_t)s * tp.stage_bytes;
           const int x = kc * tp.kc;
-          mbar_expect_tx(&full[s], tp.stage_tx);
-          tma_load_2d(st, &map_dist, x, p0, &full[s]);
-          for (int c = 0; c < 3; ++c)
-            tma_load_2d(st + (size_t)(tp.crow + c * GRP) * ROWB, &map_rad, x, c * k.P + p0, &full[s]);
-          tma_load_2d(st + tp.off_wc, &map_wc, x, 0, &full[s]);
-          tma_load_2d(st + tp.off_wv, &map_wv, x, 0, &full[s]);
-          if (kSplitW) {
-            tma_load_2d(st + tp.off_wc_lo, &map_wc_lo, x, 0, &full[s]);
-            tma_load_2d(st + tp.off_wv_lo, &map_wv_lo, x, 0, &full[s]);
+          mbar_expect_tx(&full[s], real ? tp.stage_tx : tp.w_tx);
+          if (real) {
+            tma_load_2d(st, &map_dist, x, p0, &full[s]);
+            for (int c = 0; c < 3; ++c)
+              tma_load_2d(st + (size_t)(tp.crow + c * GRP) * ROWB, &map_rad, x, c * k.P + p0, &full[s]);
+          }
+          // weight rows: visibility texels from tile row 0, colour texels from row vb
+          uint8_t* wv = st + tp.off_w;
+          uint8_t* wc = st + tp.off_w + (size_t)tp.vb * ROWB;
+          uint8_t* wv_lo = st + tp.off_w_lo;
+          uint8_t* wc_lo = st + tp.off_w_lo + (size_t)tp.vb * ROWB;
+          if (tp.cluster == 1) {
+            tma_load_2d(wv, &map_wv, x, 0, &full[s]);
+            tma_load_2d(wc, &map_wc, x, 0, &full[s]);
+            if (kSplitW) {
+              tma_load_2d(wv_lo, &map_wv_lo, x, 0, &full[s]);
+              tma_load_2d(wc_lo, &map_wc_lo, x, 0, &full[s]);
+            }
+          } else if ((uint32_t)(kc % tp.cluster) == crank) {
+            tma_load_2d_mc(wv, &map_wv, x, 0, &full[s], cmask);
+            tma_load_2d_mc(wc, &map_wc, x, 0, &full[s], cmask);
+            if (kSplitW) {
+              tma_load_2d_mc(wv_lo, &map_wv_lo, x, 0, &full[s], cmask);
+              tma_load_2d_mc(wc_lo, &map_wc_lo, x, 0, &full[s], cmask);
+            }
           }
           if (++s == tp.stages) {
             s = 0;
             ph ^= 1;
           }
+        }
+      }
+      // drain: every peer's release of every stage has arrived here before the
+      // cluster may exit
+      for (int i = 0; i < tp.stages && ok && tp.cluster > 1; ++i) {
+        ok = mbar_wait(&empty[s], ph ^ 1, err);
+        if (++s == tp.stages) {
+          s = 0;
+          ph ^= 1;
         }
       }
     }
@@ -514,10 +626,13 @@ __global__ void __launch_bounds__(NT, 1)
       int s = 0, b = 0;
       uint32_t ph = 0, tph = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < tp.items && ok; item += gridDim.x) {
-        ok = mbar_wait(&tempty[b], tph ^ 1, err);
-        if (!ok) break;
-        tc_fence_after();
+      for (int it = 0; it < tp.iters && ok; ++it) {
+        const bool real = blockIdx.x + it * gridDim.x < tp.items;
+        if (real) {
+          ok = mbar_wait(&tempty[b], tph ^ 1, err);
+          if (!ok) break;
+          tc_fence_after();
+        }
         const uint32_t dbase = tmem + b * 256;
         for (int kc = 0; kc < tp.nchunks; ++kc) {
           ok = mbar_wait(&conv[s], ph, err);
@@ -525,38 +640,32 @@ __global__ void __launch_bounds__(NT, 1)
           tc_fence_after();
           uint8_t* st = smem + (size_t)s * tp.stage_bytes;
 #pragma unroll
-          for (int ks = 0; ks < ROWB / 32; ++ks) {     // one MMA K step per 32 bytes of row
+          for (int ks = 0; ks < ROWB / 32 && real; ++ks) {   // one MMA K step per 32 bytes of row
             const int kb = ks * 32;
             const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t bx = sdesc<ROWB>(st + kb);                          // d | d^2
-            const uint64_t bl = sdesc<ROWB>(st + 2 * GRP * ROWB + kb);        // d^2 lo
-            const uint64_t bc = sdesc<ROWB>(st + (size_t)tp.crow * ROWB + kb);   // R | G | B
-            for (int j = 0; j < tp.ntv; ++j) {
-              const uint32_t dv = dbase + 64 * j;
-              const uint64_t av = sdesc<ROWB>(st + tp.off_wv + (size_t)j * MT * ROWB + kb);
-              mma<FORM>(dv, av, bx, tp.idesc64, acc);
-              if (!kSplitA) mma<FORM>(dv + GRP, av, bl, tp.idesc32, 1u);
-              if (kSplitW)
-                mma<FORM>(dv, sdesc<ROWB>(st + tp.off_wv_lo + (size_t)j * MT * ROWB + kb), bx, tp.idesc64, 1u);
-              if (kSplitA) mma<FORM>(dv, av, sdesc<ROWB>(st + tp.off_a_lo + kb), tp.idesc64, 1u);
-            }
-            for (int j = 0; j < tp.ntc; ++j) {
-              const uint32_t dc = dbase + 64 * tp.ntv + 96 * j;
-              const uint64_t ac = sdesc<ROWB>(st + tp.off_wc + (size_t)j * MT * ROWB + kb);
-              mma<FORM>(dc, ac, bc, tp.idesc96, acc);
-              if (kSplitW)
-                mma<FORM>(dc, sdesc<ROWB>(st + tp.off_wc_lo + (size_t)j * MT * ROWB + kb), bc, tp.idesc96, 1u);
-              if (kSplitA)
-                mma<FORM>(dc, ac, sdesc<ROWB>(st + tp.off_a_lo + (size_t)tp.crow * ROWB + kb), tp.idesc96, 1u);
+            // one MMA per tile (per weight / ray part): visibility tiles take the
+            // visibility rows of the ray tile, colour tiles the colour rows, a
+            // tile holding both takes the whole ray tile
+            for (int j = 0; j < tp.ntiles; ++j) {
+              const uint32_t d = dbase + tp.tbase[j];
+              const size_t brow = tp.tkind[j] == kTileCol ? (size_t)tp.crow : 0;
+              const uint64_t a = sdesc<ROWB>(st + tp.off_w + (size_t)j * MT * ROWB + kb);
+              const uint64_t bb = sdesc<ROWB>(st + brow * ROWB + kb);
+              mma<FORM>(d, a, bb, tp.tidesc[j], acc);
+              if (kSplitW) mma<FORM>(d, sdesc<ROWB>(st + tp.off_w_lo + (size_t)j * MT * ROWB + kb), bb, tp.tidesc[j], 1u);
+              if (kSplitA) mma<FORM>(d, a, sdesc<ROWB>(st + tp.off_a_lo + brow * ROWB + kb), tp.tidesc[j], 1u);
             }
           }
-          mma_commit(&empty[s]);                       // stage free once these MMAs finish
+          // stage free (in every CTA of the cluster) once these MMAs finish
+          if (tp.cluster > 1) mma_commit_mc(&empty[s], cmask);
+          else mma_commit(&empty[s]);
           if (++s == tp.stages) {
             s = 0;
             ph ^= 1;
           }
         }
         if (!ok) break;
+        if (!real) continue;
         mma_commit(&tfull[b]);                         // accumulators ready for the epilogue
         if (++b == tp.nbuf) {
           b = 0;
@@ -570,7 +679,7 @@ __global__ void __launch_bounds__(NT, 1)
     int s = 0;
     uint32_t ph = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < tp.items && ok; item += gridDim.x) {
+    for (int it = 0; it < tp.iters && ok; ++it) {
       for (int kc = 0; kc < tp.nchunks; ++kc) {
         ok = mbar_wait(&full[s], ph, err);
         if (!ok) break;
@@ -603,32 +712,27 @@ __global__ void __launch_bounds__(NT, 1)
             *(float4*)(st + tp.off_a_lo + (size_t)(ct + 64 * u) * 16) = lo;
           }
         } else {
-          // d^2 = hi + lo in the operand format (binary16 scaled by 2^-8)
+          // d^2 = hi + lo in the operand format (binary16 scaled by 2^-4): the low
+          // part keeps the rounding of d^2 out of the visibility moments
           for (int q = ct; q < GRP * CPR; q += 64) {
             const uint4 raw = *(const uint4*)(st + (size_t)q * 16);
             const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
             uint32_t oh[4], ol[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              float d0, d1;
               if constexpr (FORM == kF16) {
                 const __half2 h2 = *reinterpret_cast<const __half2*>(&w[e]);
-                d0 = __low2float(h2);
-                d1 = __high2float(h2);
-              } else {
-                const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&w[e]);
-                d0 = __low2float(h2);
-                d1 = __high2float(h2);
-              }
-              const float sc = FORM == kF16 ? 0.00390625f : 1.0f;
-              const float q0 = d0 * d0 * sc, q1 = d1 * d1 * sc;
-              if constexpr (FORM == kF16) {
+                const float d0 = __low2float(h2), d1 = __high2float(h2);
+                const float q0 = d0 * d0 * kD2ScaleF16, q1 = d1 * d1 * kD2ScaleF16;
                 const __half h0 = __float2half_rn(q0), h1 = __float2half_rn(q1);
                 const __half l0 = __float2half_rn(q0 - __half2float(h0));
                 const __half l1 = __float2half_rn(q1 - __half2float(h1));
                 oh[e] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
                 ol[e] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
               } else {
+                const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&w[e]);
+                const float d0 = __low2float(h2), d1 = __high2float(h2);
+                const float q0 = d0 * d0, q1 = d1 * d1;
                 const __nv_bfloat16 h0 = __float2bfloat16_rn(q0), h1 = __float2bfloat16_rn(q1);
                 const __nv_bfloat16 l0 = __float2bfloat16_rn(q0 - __bfloat162float(h0));
                 const __nv_bfloat16 l1 = __float2bfloat16_rn(q1 - __bfloat162float(h1));
@@ -675,12 +779,30 @@ __global__ void __launch_bounds__(NT, 1)
     if (e < 4) flag_mask[e] = 0;
     epi_bar();
     const float h = *k.hy, omh = 1.0f - h;
-    const float d2_scale = FORM == kF16 ? 256.0f : 1.0f;
+    constexpr bool kSplitD2 = FORM != kF32;         // d^2 as hi + lo columns
     const int kind = k.color_code;
     const bool f16 = k.state_fmt == PV_FMT_F16;
     const uint32_t s_st_c = smem_u32(st_c), s_st_v = smem_u32(st_v);
     const uint32_t s_ls_c = smem_u32(ls_c), s_ls_v = smem_u32(ls_v);
     const uint32_t s_rsum = smem_u32(rsum), s_pos = smem_u32(tab_pos), s_gb = smem_u32(gb);
+    EpiCtx x;
+    x.s_rsum = s_rsum;
+    x.s_pos = s_pos;
+    x.s_st_c = s_st_c;
+    x.s_st_v = s_st_v;
+    x.s_ls_c = s_ls_c;
+    x.s_ls_v = s_ls_v;
+    x.sc_stride = k.sc_stride;
+    x.sv_stride = k.sv_stride;
+    x.lc_stride = k.lc_stride;
+    x.lv_stride = k.lv_stride;
+    x.Tc = k.Tc;
+    x.Tv = k.Tv;
+    x.np = np;
+    x.npi = np;
+    x.h = h;
+    x.omh = omh;
+    x.d2_scale = FORM == kF16 ? 1.0f / kD2ScaleF16 : 1.0f;
     int b = 0, par = 0;
     uint32_t tph = 0, eph = 0;
     bool ok = true;
@@ -692,28 +814,15 @@ __global__ void __launch_bounds__(NT, 1)
       if (!ok) break;
       eph ^= 1;
       tc_fence_after();
-      const uint32_t tcol = tmem + ((uint32_t)(quarter * 32) << 16) + b * 256;
-      const uint32_t tcol_c = tcol + 64 * tp.ntv;
-      int task = 0;
+      const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + b * 256;
+      x.npi = npi;
       uint32_t mv, mc;
       if (f16) {
-        mv = epi_texture<0, 0, true>(tcol, tp.ntv, k.Tv, quarter, slot, lane, task, s_rsum + 4u * k.Tc, s_pos + 2u * k.Tc,
-                                     s_st_v, k.sv_stride, s_ls_v, k.lv_stride, np, npi, h, omh, d2_scale);
-        if (kind == PV_CODE_UNORM10)
-          mc = epi_texture<0, PV_CODE_UNORM10, false>(tcol_c, tp.ntc, k.Tc, quarter, slot, lane, task, s_rsum, s_pos,
-                                                      s_st_c, k.sc_stride, s_ls_c, k.lc_stride, np, npi, h, omh, 1.0f);
-        else
-          mc = epi_texture<0, PV_CODE_UF10, false>(tcol_c, tp.ntc, k.Tc, quarter, slot, lane, task, s_rsum, s_pos,
-                                                   s_st_c, k.sc_stride, s_ls_c, k.lc_stride, np, npi, h, omh, 1.0f);
+        if (kind == PV_CODE_UNORM10) epi_item<0, PV_CODE_UNORM10, kSplitD2>(tp, x, tq, quarter, lane, slot, mc, mv);
+        else epi_item<0, PV_CODE_UF10, kSplitD2>(tp, x, tq, quarter, lane, slot, mc, mv);
       } else {
-        mv = epi_texture<1, 0, true>(tcol, tp.ntv, k.Tv, quarter, slot, lane, task, s_rsum + 4u * k.Tc, s_pos + 2u * k.Tc,
-                                     s_st_v, k.sv_stride, s_ls_v, k.lv_stride, np, npi, h, omh, d2_scale);
-        if (kind == PV_CODE_UNORM10)
-          mc = epi_texture<1, PV_CODE_UNORM10, false>(tcol_c, tp.ntc, k.Tc, quarter, slot, lane, task, s_rsum, s_pos,
-                                                      s_st_c, k.sc_stride, s_ls_c, k.lc_stride, np, npi, h, omh, 1.0f);
-        else
-          mc = epi_texture<1, PV_CODE_UF10, false>(tcol_c, tp.ntc, k.Tc, quarter, slot, lane, task, s_rsum, s_pos,
-                                                   s_st_c, k.sc_stride, s_ls_c, k.lc_stride, np, npi, h, omh, 1.0f);
+        if (kind == PV_CODE_UNORM10) epi_item<1, PV_CODE_UNORM10, kSplitD2>(tp, x, tq, quarter, lane, slot, mc, mv);
+        else epi_item<1, PV_CODE_UF10, kSplitD2>(tp, x, tq, quarter, lane, slot, mc, mv);
       }
       // accumulators consumed: hand the TMEM buffer back to the MMA thread
       tc_fence_before();
@@ -765,8 +874,13 @@ __global__ void __launch_bounds__(NT, 1)
     if (e == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
 
+  // After a timeout a peer's last weight multicast may still be in flight
+  // towards this CTA: give it time to land before the cluster may exit.
+  if (tp.cluster > 1 && *(volatile int*)err)
+    for (int i = 0; i < 64; ++i) __nanosleep(1000);
   tc_fence_before();
-  __syncthreads();
+  if (tp.cluster > 1) cluster_sync();               // no peer still writes into this CTA
+  else __syncthreads();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
@@ -822,6 +936,39 @@ uint32_t make_idesc(int form, int M, int N) {
 
 size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
+cudaError_t set_smem_attr(int form, int bytes) {
+  if (form == kF16) return cudaFuncSetAttribute(k_blend_tc<kF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (form == kBF16)
+    return cudaFuncSetAttribute(k_blend_tc<kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(k_blend_tc<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// Clusters of `cluster` CTAs (one CTA per SM) that fit on the GPU at once; 0
+// if the query fails.
+int max_clusters(int form, int cluster, int smem) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e;
+  if (form == kF16) e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kF16>, &cfg);
+  else if (form == kBF16) e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kBF16>, &cfg);
+  else e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kF32>, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 }  // namespace
 
 bool pv_tc_supported(const pv_desc* d, const char** why) {
@@ -871,47 +1018,77 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   const int ROWB = form == kF32 ? row_bytes<kF32>() : row_bytes<kF16>();
   tp.kc = ROWB / ob;
   tp.nchunks = (k.R + tp.kc - 1) / tp.kc;
-  tp.ntc = (k.Tc + MT - 1) / MT;
-  tp.ntv = (k.Tv + MT - 1) / MT;
-  tp.bufcols = 64 * tp.ntv + 96 * tp.ntc;
+  // ray (B) tile rows: d | d^2 (| d^2 lo, 16-bit forms) | R | G | B, 32 each
+  tp.nvc = form != kF32 ? 3 * GRP : 2 * GRP;
+  tp.crow = tp.nvc;
+  tp.a_rows = tp.crow + 3 * GRP;
+  // texel (A) tiles: visibility texels in rows 0..Tv-1, colour texels from
+  // row vb (8-row aligned, so that their TMA destination stays aligned); one
+  // MMA per 128-row tile, with the B rows its texels need
+  tp.vbox = (k.Tv + 7) / 8 * 8;
+  tp.cbox = (k.Tc + 7) / 8 * 8;
+  tp.vb = tp.vbox;
+  const int rows = tp.vb + tp.cbox;
+  tp.ntiles = (rows + MT - 1) / MT;
+  int col = 0;
+  for (int j = 0; j < tp.ntiles; ++j) {
+    const int r0 = j * MT, r1 = r0 + MT;
+    const bool has_v = r0 < k.Tv, has_c = r1 > tp.vb && r0 < tp.vb + k.Tc;
+    tp.tkind[j] = has_v && has_c ? kTileBoth : (has_v ? kTileVis : kTileCol);
+    const int n = tp.tkind[j] == kTileBoth ? tp.a_rows : (tp.tkind[j] == kTileVis ? tp.nvc : 3 * GRP);
+    tp.tbase[j] = col;
+    tp.tidesc[j] = make_idesc(form, MT, n);
+    col += n;
+  }
+  tp.bufcols = col;
   tp.nbuf = tp.bufcols <= 256 ? 2 : 1;         // buffers at TMEM columns 0 and 256
-  tp.a_rows = form == kF32 ? 160 : 192;
-  tp.crow = form == kF32 ? 64 : 96;
   tp.gb_c = 4 * k.nc + 4;
   tp.gb_v = 4 * k.nv + 4;
-  // stage layout: ray tile, its TF32 low parts, then the weight planes. A
-  // weight plane holds only the texture's rows (tc_pad / tv_pad of them), but
-  // its MMAs read whole 128-row tiles: the rows past the plane read whatever
-  // follows (the lanes they produce are ignored); `guard` keeps those reads
-  // of the last stage inside the allocation.
+  // stage layout: ray tile, its TF32 low parts (FP32 form), then the weight
+  // tile(s): ntiles * 128 rows each, of which the MMAs read all (rows past
+  // the texels hold whatever was there; the lanes they produce are ignored)
   size_t off = 0;
   const size_t a_b = align1k((size_t)tp.a_rows * ROWB);
   off += a_b;
   tp.off_a_lo = (int)off;
   if (form == kF32) off += a_b;
-  size_t ext = 0;
-  auto plane = [&](int rows, int ntiles) {
-    const size_t o = off;
-    off += align1k((size_t)rows * ROWB);
-    const size_t end = o + (size_t)ntiles * MT * ROWB;
-    ext = end > ext ? end : ext;
-    return (int)o;
-  };
-  tp.off_wc = plane(k.tc_pad, tp.ntc);
-  tp.off_wv = plane(k.tv_pad, tp.ntv);
-  tp.off_wc_lo = tp.off_wc;
-  tp.off_wv_lo = tp.off_wv;
+  const size_t w_b = (size_t)tp.ntiles * MT * ROWB;
+  tp.off_w = (int)off;
+  off += w_b;
+  tp.off_w_lo = tp.off_w;
   if (form != kF16) {
-    tp.off_wc_lo = plane(k.tc_pad, tp.ntc);
-    tp.off_wv_lo = plane(k.tv_pad, tp.ntv);
+    tp.off_w_lo = (int)off;
+    off += w_b;
   }
   tp.stage_bytes = (int)off;
-  const size_t guard = ext > off ? align1k(ext - off) : 0;
-  // probes per work item: one item per SM where possible, fewer probes when
-  // the item's tiles would leave room for less than two stages
+  // Clusters of `cluster` CTAs can share each weight chunk (multicast); the
+  // grid is the number of CTAs that can be resident at once, in whole
+  // clusters. Measured on GB300 at 16^3 probes x 256 rays, sharing gains
+  // nothing there (the weight tiles come from L2 and the MMAs, not the loads,
+  // bound the main loop), so one CTA per cluster is the default;
+  // PV_TC_CLUSTER=2|4|8 selects sharing.
+  int cluster = 1;
+  if (const char* env = getenv("PV_TC_CLUSTER")) {
+    const int c = atoi(env);
+    if (c == 1 || c == 2 || c == 4 || c == 8) cluster = c;
+  }
+  e = set_smem_attr(form, smem_max);
+  if (e != cudaSuccess) {
+    delete pl;
+    return e;
+  }
+  int resident = sms;
+  if (cluster > 1) {
+    const int nc = max_clusters(form, cluster, smem_max);
+    if (nc > 0) resident = nc * cluster;
+    else cluster = 1;
+  }
+  tp.cluster = cluster;
+  // probes per work item: one item per resident CTA where possible, fewer
+  // probes when the item's tiles would leave room for less than two stages
   const size_t n_rsum = (size_t)(k.Tc + k.Tv) * 4, n_pos = (size_t)(k.Tc + k.Tv) * 2;
   const size_t n_gb = (size_t)(tp.gb_c + tp.gb_v) * 4;
-  int np = (k.P + sms - 1) / sms;
+  int np = (k.P + resident - 1) / resident;
   np = np < 1 ? 1 : (np > np_max ? np_max : np);
   int stages = 0;
   size_t epi_state = 0, epi_last = 0;
@@ -922,7 +1099,7 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
     epi_last = ((size_t)np * (3 * k.lc_stride + 2 * k.lv_stride) + 8 * (size_t)k.lv_stride) * 2;
     const size_t epi = align1k(epi_state) + align1k(epi_last) + align1k(n_rsum) + align1k(n_pos) +
                        align1k(n_gb) + 1024 + 1024;
-    const size_t need = 1024 + epi + guard;
+    const size_t need = 1024 + epi;
     stages = need < (size_t)smem_max ? (int)(((size_t)smem_max - need) / tp.stage_bytes) : 0;
     if (stages >= 2) break;
   }
@@ -933,10 +1110,13 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   if (stages > 4) stages = 4;
   tp.np = np;
   tp.items = (k.P + np - 1) / np;
-  pl->grid = tp.items < sms ? tp.items : sms;
+  const int want = (tp.items + cluster - 1) / cluster * cluster;
+  pl->grid = want < resident ? want : resident;
+  tp.iters = (tp.items + pl->grid - 1) / pl->grid;
   tp.stages = stages;
-  tp.stage_tx = (uint32_t)((4 * np + (form != kF16 ? 2 : 1) * (k.tc_pad + k.tv_pad)) * ROWB);
-  off = (size_t)stages * tp.stage_bytes + guard;
+  tp.w_tx = (uint32_t)((form != kF16 ? 2 : 1) * (tp.vbox + tp.cbox) * ROWB);
+  tp.stage_tx = (uint32_t)(4 * np * ROWB) + tp.w_tx;
+  off = (size_t)stages * tp.stage_bytes;
   tp.off_state = (int)off;
   off += align1k(epi_state);
   tp.off_last = (int)off;
@@ -952,33 +1132,22 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   tp.off_bar = (int)off;
   off += 1024;
   pl->smem = off + 1024;                       // slack for aligning the dynamic base
-  tp.idesc32 = make_idesc(form, MT, 32);
-  tp.idesc64 = make_idesc(form, MT, 64);
-  tp.idesc96 = make_idesc(form, MT, 96);
   // weight tensor maps (fixed for the volume's life)
   const size_t wplane = (size_t)(k.tc_pad + k.tv_pad) * k.r_pad;
   const uint8_t* w = (const uint8_t*)k.w_op;
-  e = encode_2d(&pl->wc, k.operand_fmt, w, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc, k.tc_pad);
+  e = encode_2d(&pl->wc, k.operand_fmt, w, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.cbox);
   if (e == cudaSuccess)
     e = encode_2d(&pl->wv, k.operand_fmt, w + (size_t)k.tc_pad * k.r_pad * ob, k.r_pad, k.tv_pad,
-                  (uint64_t)k.r_pad * ob, tp.kc, k.tv_pad);
+                  (uint64_t)k.r_pad * ob, tp.kc, tp.vbox);
   if (e == cudaSuccess && form != kF16) {
     e = encode_2d(&pl->wc_lo, k.operand_fmt, w + wplane * ob, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob,
-                  tp.kc, k.tc_pad);
+                  tp.kc, tp.cbox);
     if (e == cudaSuccess)
       e = encode_2d(&pl->wv_lo, k.operand_fmt, w + (wplane + (size_t)k.tc_pad * k.r_pad) * ob, k.r_pad,
-                    k.tv_pad, (uint64_t)k.r_pad * ob, tp.kc, k.tv_pad);
+                    k.tv_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.vbox);
   } else {
     pl->wc_lo = pl->wc;
     pl->wv_lo = pl->wv;
-  }
-  if (e == cudaSuccess) {
-    if (form == kF16)
-      e = cudaFuncSetAttribute(k_blend_tc<kF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
-    else if (form == kBF16)
-      e = cudaFuncSetAttribute(k_blend_tc<kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
-    else
-      e = cudaFuncSetAttribute(k_blend_tc<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
   }
   if (e != cudaSuccess) {
     delete pl;
@@ -1008,16 +1177,28 @@ cudaError_t pv_launch_blend_tc(pv_volume* v, const void* rad, const void* dist, 
   if (e != cudaSuccess) return e;
   TcParams tp = pl->tp;
   tp.k = k;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = tp.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(pl->grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = pl->smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   switch (pl->form) {
     case kF16:
-      k_blend_tc<kF16><<<pl->grid, NT, pl->smem, st>>>(tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
+      e = cudaLaunchKernelEx(&cfg, k_blend_tc<kF16>, tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
       break;
     case kBF16:
-      k_blend_tc<kBF16><<<pl->grid, NT, pl->smem, st>>>(tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
+      e = cudaLaunchKernelEx(&cfg, k_blend_tc<kBF16>, tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
       break;
     default:
-      k_blend_tc<kF32><<<pl->grid, NT, pl->smem, st>>>(tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
+      e = cudaLaunchKernelEx(&cfg, k_blend_tc<kF32>, tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
       break;
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
