@@ -255,6 +255,46 @@ pv_status probe_update_static(const pv_desc* desc, uint64_t frame, const void* r
                               const float* dirs, void* tiles_c, void* tiles_v, const uint16_t* last_c,
                               const uint16_t* last_v, uint32_t* changed_bits, void* stream);
 
+/* ----------------------------------------------------------------- batches */
+/*
+ * Batched form: up to PV_MAX_BATCH volumes with equal tile interiors, state
+ * and operand formats and colour code (probe grids and rays per probe may
+ * differ), all using the tensor-core blend, updated together: the weights of
+ * every volume in one launch, the blend of every volume in one persistent
+ * launch over all of their work items (np probes each, one CTA per SM), and
+ * the selection and packing of every volume in one launch. Results equal
+ * those of the same calls made volume by volume. The batch refers to the
+ * volumes; they must outlive it and be used only through it while it is in
+ * use. All entry points except probe_batch_tune are asynchronous on `stream`
+ * and can be captured in a CUDA graph (kernel arguments are fixed at capture).
+ *  probe_batch_create   vols[n]; probes_per_item 0 picks np from the probe
+ *                       count and the SM count, otherwise np (clamped to what
+ *                       fits). Errors: PV_ERR_INVALID (mixed shapes, NULL,
+ *                       duplicates), PV_ERR_RANGE (n > PV_MAX_BATCH),
+ *                       PV_ERR_UNSUPPORTED (a volume without the tensor-core
+ *                       blend), PV_ERR_CUDA.
+ *  probe_batch_update   radiance[n], dist[n], dirs[n]: device inputs of each
+ *                       volume as for probe_update.
+ *  probe_batch_select_and_pack   out: host array of n pv_frame (device
+ *                       counts only: count_c / count_v are -1).
+ *  probe_batch_tune     times the blend for candidate np (8..32) with these
+ *                       inputs, `reps` launches each, and keeps the fastest;
+ *                       the volumes' tiles, changed bits, frame counters and
+ *                       hysteresis are restored afterwards. Synchronises the
+ *                       stream; out_probes_per_item (may be NULL) gets np.
+ *  probe_batch_info     the batch's current np.
+ */
+#define PV_MAX_BATCH 16
+typedef struct pv_batch pv_batch;
+pv_status probe_batch_create(pv_volume* const* vols, int32_t n, int32_t probes_per_item, pv_batch** out);
+pv_status probe_batch_destroy(pv_batch* batch);
+pv_status probe_batch_info(const pv_batch* batch, int32_t* probes_per_item);
+pv_status probe_batch_update(pv_batch* batch, const void* const* radiance, const void* const* dist,
+                             const float* const* dirs, void* stream);
+pv_status probe_batch_select_and_pack(pv_batch* batch, pv_frame* out, void* stream);
+pv_status probe_batch_tune(pv_batch* batch, const void* const* radiance, const void* const* dist,
+                           const float* const* dirs, int32_t reps, int32_t* out_probes_per_item, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

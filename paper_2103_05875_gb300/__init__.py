@@ -85,6 +85,12 @@ def _load():
         "probe_volume_export_state": (i32, [vp, vp, vp, vp, vp, C.POINTER(u64), vp]),
         "probe_volume_import_state": (i32, [vp, vp, vp, vp, vp, u64, vp]),
         "probe_update_static": (i32, [C.POINTER(pv_desc), u64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "probe_batch_create": (i32, [C.POINTER(vp), i32, i32, C.POINTER(vp)]),
+        "probe_batch_destroy": (i32, [vp]),
+        "probe_batch_info": (i32, [vp, C.POINTER(i32)]),
+        "probe_batch_update": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]),
+        "probe_batch_select_and_pack": (i32, [vp, C.POINTER(pv_frame), vp]),
+        "probe_batch_tune": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(i32), vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -230,6 +236,48 @@ def probe_update_static(desc: pv_desc, frame: int, radiance, dist, dirs, tiles_c
 
 
 # ------------------------------------------------------------------ device views
+def _ptr_array(items):
+    arr = (C.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = _ptr(t)
+    return arr
+
+
+def probe_batch_create(vols, probes_per_item: int = 0) -> int:
+    arr = _ptr_array(vols)
+    out = C.c_void_p()
+    _check(lib.probe_batch_create(arr, len(vols), int(probes_per_item), C.byref(out)), "probe_batch_create")
+    return out.value
+
+
+def probe_batch_destroy(batch: int):
+    _check(lib.probe_batch_destroy(batch), "probe_batch_destroy")
+
+
+def probe_batch_info(batch: int) -> int:
+    n = C.c_int32()
+    _check(lib.probe_batch_info(batch, C.byref(n)), "probe_batch_info")
+    return n.value
+
+
+def probe_batch_update(batch: int, radiance, dist, dirs, stream=None):
+    _check(lib.probe_batch_update(batch, _ptr_array(radiance), _ptr_array(dist), _ptr_array(dirs), _stream(stream)),
+           "probe_batch_update")
+
+
+def probe_batch_select_and_pack(batch: int, n: int, stream=None):
+    out = (pv_frame * n)()
+    _check(lib.probe_batch_select_and_pack(batch, out, _stream(stream)), "probe_batch_select_and_pack")
+    return list(out)
+
+
+def probe_batch_tune(batch: int, radiance, dist, dirs, reps: int = 3, stream=None) -> int:
+    n = C.c_int32()
+    _check(lib.probe_batch_tune(batch, _ptr_array(radiance), _ptr_array(dist), _ptr_array(dirs), int(reps),
+                                C.byref(n), _stream(stream)), "probe_batch_tune")
+    return n.value
+
+
 class _DeviceArray:
     """Exposes a device pointer to torch through __cuda_array_interface__ (no copy)."""
 
@@ -317,3 +365,36 @@ class ProbeVolume:
     def import_state(self, tiles_c, tiles_v, last_c, last_v, frame: int, stream=None):
         probe_volume_import_state(self.handle, tiles_c.contiguous(), tiles_v.contiguous(),
                                   last_c.contiguous(), last_v.contiguous(), frame, stream)
+
+
+class ProbeBatch:
+    """Several ProbeVolumes of equal tile shapes and formats updated together
+    (see probe_batch_create). The volumes must outlive the batch."""
+
+    def __init__(self, volumes, probes_per_item: int = 0):
+        self.volumes = list(volumes)
+        self.handle = probe_batch_create([v.handle for v in self.volumes], probes_per_item)
+
+    @property
+    def probes_per_item(self) -> int:
+        return probe_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            probe_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, radiance, dist, dirs, stream=None):
+        probe_batch_update(self.handle, radiance, dist, dirs, stream)
+
+    def select_and_pack(self, stream=None):
+        return probe_batch_select_and_pack(self.handle, len(self.volumes), stream)
+
+    def tune(self, radiance, dist, dirs, reps: int = 3, stream=None) -> int:
+        return probe_batch_tune(self.handle, radiance, dist, dirs, reps, stream)

@@ -83,7 +83,7 @@ constexpr float kD2ScaleF16 = 0.0625f;
 
 struct TcParams {
   pv_dev k;
-  int np, items, iters, stages, kc, nchunks;
+  int np, items, iters, stages, kc;
   int cluster;                           // CTAs per cluster sharing each weight chunk
   int ntiles, bufcols, nbuf;             // 128-row texel tiles; TMEM columns a buffer uses
   int vb;                                // tile row of colour texel 0 (visibility texels: rows 0..Tv-1)
@@ -98,6 +98,31 @@ struct TcParams {
   int gb_c, gb_v;                        // guard-band texels per tile: 4n + 4
   uint32_t stage_tx, w_tx;               // bytes per stage: all, weight tiles only
 };
+
+// One volume of a launch: its tensor maps, its buffers and its work items.
+// Every volume of a launch shares the tile shapes, state and operand formats
+// (the fields of TcParams); rays and probe counts may differ.
+struct BlendVol {
+  CUtensorMap rad, dist, wc, wv, wc_lo, wv_lo;
+  pv_dev k;
+  int item0;                             // first work item of the volume in the launch
+  int nchunks;                           // ray chunks of kc rays
+};
+
+template <int MAXV>
+struct BlendArgs {
+  TcParams tp;                           // tp.k: shape of the volumes, error word
+  int nvol;
+  BlendVol v[MAXV];
+};
+
+// Volume of global work item `item` (items are numbered volume by volume).
+template <int MAXV>
+__device__ __forceinline__ int vol_of(const BlendArgs<MAXV>& a, int item) {
+  int v = 0;
+  while (v + 1 < a.nvol && item >= a.v[v + 1].item0) ++v;
+  return v;
+}
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -484,15 +509,12 @@ __device__ __forceinline__ int ring_slot(int r, int c, int n) {
 }
 
 // ------------------------------------------------------------------ kernel
-template <int FORM>
-__global__ void __launch_bounds__(NT, 1)
-    k_blend_tc(const __grid_constant__ TcParams tp, const __grid_constant__ CUtensorMap map_rad,
-               const __grid_constant__ CUtensorMap map_dist, const __grid_constant__ CUtensorMap map_wc,
-               const __grid_constant__ CUtensorMap map_wv, const __grid_constant__ CUtensorMap map_wc_lo,
-               const __grid_constant__ CUtensorMap map_wv_lo) {
+template <int FORM, int MAXV>
+__global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ BlendArgs<MAXV> a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const pv_dev& k = tp.k;
+  const TcParams& tp = a.tp;
+  const pv_dev& k = tp.k;                          // shapes and formats shared by the volumes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool kSplitW = FORM != kF16;
   constexpr bool kSplitA = FORM == kF32;
@@ -549,17 +571,22 @@ __global__ void __launch_bounds__(NT, 1)
   int* err = k.err;
   const uint32_t crank = tp.cluster > 1 ? cluster_rank() : 0u;
   const uint16_t cmask = (uint16_t)((1u << tp.cluster) - 1u);
+  // rounds of this CTA: its items, or (clusters) the cluster's common count
+  const int rounds = tp.cluster > 1 ? tp.iters
+                                    : (tp.items > (int)blockIdx.x ? (tp.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&map_dist) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&map_rad) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&map_wc) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&map_wv) : "memory");
-      if (kSplitW) {
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&map_wc_lo) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&map_wv_lo) : "memory");
+      for (int v = 0; v < a.nvol; ++v) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].dist) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].rad) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].wc) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].wv) : "memory");
+        if (kSplitW) {
+          asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].wc_lo) : "memory");
+          asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].wv_lo) : "memory");
+        }
       }
       int s = 0;
       uint32_t ph = 0;
@@ -569,20 +596,21 @@ __global__ void __launch_bounds__(NT, 1)
       // multicasts and the stages it frees keep its peers going). Chunk kc's
       // weight tiles are loaded once per cluster, by rank kc % cluster, into
       // every CTA's stage.
-      for (int it = 0; it < tp.iters && ok; ++it) {
+      for (int it = 0; it < rounds && ok; ++it) {
         const int item = blockIdx.x + it * gridDim.x;
         const bool real = item < tp.items;
-        const int p0 = item * np;
-        for (int kc = 0; kc < tp.nchunks; ++kc) {
+        const BlendVol& bv = a.v[vol_of(a, real ? item : tp.items - 1)];
+        const int p0 = (item - bv.item0) * np;
+        for (int kc = 0; kc < bv.nchunks; ++kc) {
           ok = mbar_wait(&empty[s], ph ^ 1, err);
           if (!ok) break;
           uint8_t* st = smem + (size_t)s * tp.stage_bytes;
           const int x = kc * tp.kc;
           mbar_expect_tx(&full[s], real ? tp.stage_tx : tp.w_tx);
           if (real) {
-            tma_load_2d(st, &map_dist, x, p0, &full[s]);
+            tma_load_2d(st, &bv.dist, x, p0, &full[s]);
             for (int c = 0; c < 3; ++c)
-              tma_load_2d(st + (size_t)(tp.crow + c * GRP) * ROWB, &map_rad, x, c * k.P + p0, &full[s]);
+              tma_load_2d(st + (size_t)(tp.crow + c * GRP) * ROWB, &bv.rad, x, c * bv.k.P + p0, &full[s]);
           }
           // weight rows: visibility texels from tile row 0, colour texels from row vb
           uint8_t* wv = st + tp.off_w;
@@ -590,18 +618,18 @@ __global__ void __launch_bounds__(NT, 1)
           uint8_t* wv_lo = st + tp.off_w_lo;
           uint8_t* wc_lo = st + tp.off_w_lo + (size_t)tp.vb * ROWB;
           if (tp.cluster == 1) {
-            tma_load_2d(wv, &map_wv, x, 0, &full[s]);
-            tma_load_2d(wc, &map_wc, x, 0, &full[s]);
+            tma_load_2d(wv, &bv.wv, x, 0, &full[s]);
+            tma_load_2d(wc, &bv.wc, x, 0, &full[s]);
             if (kSplitW) {
-              tma_load_2d(wv_lo, &map_wv_lo, x, 0, &full[s]);
-              tma_load_2d(wc_lo, &map_wc_lo, x, 0, &full[s]);
+              tma_load_2d(wv_lo, &bv.wv_lo, x, 0, &full[s]);
+              tma_load_2d(wc_lo, &bv.wc_lo, x, 0, &full[s]);
             }
           } else if ((uint32_t)(kc % tp.cluster) == crank) {
-            tma_load_2d_mc(wv, &map_wv, x, 0, &full[s], cmask);
-            tma_load_2d_mc(wc, &map_wc, x, 0, &full[s], cmask);
+            tma_load_2d_mc(wv, &bv.wv, x, 0, &full[s], cmask);
+            tma_load_2d_mc(wc, &bv.wc, x, 0, &full[s], cmask);
             if (kSplitW) {
-              tma_load_2d_mc(wv_lo, &map_wv_lo, x, 0, &full[s], cmask);
-              tma_load_2d_mc(wc_lo, &map_wc_lo, x, 0, &full[s], cmask);
+              tma_load_2d_mc(wv_lo, &bv.wv_lo, x, 0, &full[s], cmask);
+              tma_load_2d_mc(wc_lo, &bv.wc_lo, x, 0, &full[s], cmask);
             }
           }
           if (++s == tp.stages) {
@@ -626,15 +654,17 @@ __global__ void __launch_bounds__(NT, 1)
       int s = 0, b = 0;
       uint32_t ph = 0, tph = 0;
       bool ok = true;
-      for (int it = 0; it < tp.iters && ok; ++it) {
-        const bool real = blockIdx.x + it * gridDim.x < tp.items;
+      for (int it = 0; it < rounds && ok; ++it) {
+        const int item = blockIdx.x + it * gridDim.x;
+        const bool real = item < tp.items;
+        const int nchunks = a.v[vol_of(a, real ? item : tp.items - 1)].nchunks;
         if (real) {
           ok = mbar_wait(&tempty[b], tph ^ 1, err);
           if (!ok) break;
           tc_fence_after();
         }
         const uint32_t dbase = tmem + b * 256;
-        for (int kc = 0; kc < tp.nchunks; ++kc) {
+        for (int kc = 0; kc < nchunks; ++kc) {
           ok = mbar_wait(&conv[s], ph, err);
           if (!ok) break;
           tc_fence_after();
@@ -679,8 +709,10 @@ __global__ void __launch_bounds__(NT, 1)
     int s = 0;
     uint32_t ph = 0;
     bool ok = true;
-    for (int it = 0; it < tp.iters && ok; ++it) {
-      for (int kc = 0; kc < tp.nchunks; ++kc) {
+    for (int it = 0; it < rounds && ok; ++it) {
+      const int item = blockIdx.x + it * gridDim.x;
+      const int nchunks = a.v[vol_of(a, item < tp.items ? item : tp.items - 1)].nchunks;
+      for (int kc = 0; kc < nchunks; ++kc) {
         ok = mbar_wait(&full[s], ph, err);
         if (!ok) break;
         uint8_t* st = smem + (size_t)s * tp.stage_bytes;
@@ -760,12 +792,14 @@ __global__ void __launch_bounds__(NT, 1)
     const int slot = ew >> 2;                          // which of the quarter's three warps
     // thread 0 streams each item's old texels and codes into shared memory as
     // soon as the previous item's tiles have been written back
-    if (e == 0 && blockIdx.x < tp.items) prefetch_item(k, np, blockIdx.x * np, sb, st_c, st_v, ls_c, ls_v, efull);
-    // per-texel tables, built while the first stages load
+    if (e == 0 && blockIdx.x < tp.items) {
+      const BlendVol& bv = a.v[vol_of(a, blockIdx.x)];
+      prefetch_item(bv.k, np, ((int)blockIdx.x - bv.item0) * np, sb, st_c, st_v, ls_c, ls_v, efull);
+    }
+    // per-texel tables, built while the first stages load (the weight sums,
+    // which differ per volume, when an item of a new volume starts)
     for (int t = e; t < k.Tc + k.Tv; t += EPI_THREADS) {
       const bool vis = t >= k.Tc;
-      const float S = k.sums[t];
-      rsum[t] = S > 0.0f ? 1.0f / S : 0.0f;
       const int n = vis ? k.nv : k.nc, tt = vis ? t - k.Tc : t;
       const int i = tt / n, j = tt % n;
       const int src = (i + 1) * (n + 2) + (j + 1);
@@ -777,8 +811,6 @@ __global__ void __launch_bounds__(NT, 1)
         g[ring_slot(tr[q], tc[q], n)] = (uint32_t)(tr[q] * (n + 2) + tc[q]) | ((uint32_t)src << 16);
     }
     if (e < 4) flag_mask[e] = 0;
-    epi_bar();
-    const float h = *k.hy, omh = 1.0f - h;
     constexpr bool kSplitD2 = FORM != kF32;         // d^2 as hi + lo columns
     const int kind = k.color_code;
     const bool f16 = k.state_fmt == PV_FMT_F16;
@@ -800,15 +832,25 @@ __global__ void __launch_bounds__(NT, 1)
     x.Tv = k.Tv;
     x.np = np;
     x.npi = np;
-    x.h = h;
-    x.omh = omh;
     x.d2_scale = FORM == kF16 ? 1.0f / kD2ScaleF16 : 1.0f;
-    int b = 0, par = 0;
+    int b = 0, par = 0, cur = -1;
     uint32_t tph = 0, eph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < tp.items && ok; item += gridDim.x) {
-      const int p0 = item * np;
-      const int npi = min(np, k.P - p0);
+      const int vi = vol_of(a, item);
+      const pv_dev& kv = a.v[vi].k;
+      const int p0 = (item - a.v[vi].item0) * np;      // first probe of the item in its volume
+      const int npi = min(np, kv.P - p0);
+      if (vi != cur) {                                 // this volume's weight sums and hysteresis
+        for (int t = e; t < k.Tc + k.Tv; t += EPI_THREADS) {
+          const float S = kv.sums[t];
+          rsum[t] = S > 0.0f ? 1.0f / S : 0.0f;
+        }
+        x.h = *kv.hy;
+        x.omh = 1.0f - x.h;
+        cur = vi;
+      }
+      epi_bar();
       ok = mbar_wait(efull, eph, err);
       if (ok) ok = mbar_wait(&tfull[b], tph, err);
       if (!ok) break;
@@ -843,7 +885,7 @@ __global__ void __launch_bounds__(NT, 1)
         const uint32_t m = fm[e];
         fm[e] = 0;                                     // this parity's masks are next used two items on
         const int sh = p0 & 31;
-        uint32_t* w = &k.chg[e * k.chg_words + (p0 >> 5)];
+        uint32_t* w = &kv.chg[e * kv.chg_words + (p0 >> 5)];
         if (m << sh) atomicOr(w, m << sh);
         if (sh && (m >> (32 - sh))) atomicOr(w + 1, m >> (32 - sh));
       }
@@ -860,15 +902,18 @@ __global__ void __launch_bounds__(NT, 1)
       if (e == 0) {
         const uint32_t sc_b = (uint32_t)npi * k.sc_stride * sb, sv_b = (uint32_t)npi * k.sv_stride * sb;
         for (int c = 0; c < 3; ++c)
-          bulk_s2g((uint8_t*)k.state_c + ((size_t)c * k.P + p0) * k.sc_stride * sb,
+          bulk_s2g((uint8_t*)kv.state_c + ((size_t)c * kv.P + p0) * k.sc_stride * sb,
                    st_c + (size_t)c * np * k.sc_stride * sb, sc_b);
         for (int c = 0; c < 2; ++c)
-          bulk_s2g((uint8_t*)k.state_v + ((size_t)c * k.P + p0) * k.sv_stride * sb,
+          bulk_s2g((uint8_t*)kv.state_v + ((size_t)c * kv.P + p0) * k.sv_stride * sb,
                    st_v + (size_t)c * np * k.sv_stride * sb, sv_b);
         bulk_commit();
         bulk_wait_read();                              // shared tiles may be refilled now
         const int next = item + gridDim.x;
-        if (next < tp.items) prefetch_item(k, np, next * np, sb, st_c, st_v, ls_c, ls_v, efull);
+        if (next < tp.items) {
+          const BlendVol& nv = a.v[vol_of(a, next)];
+          prefetch_item(nv.k, np, (next - nv.item0) * np, sb, st_c, st_v, ls_c, ls_v, efull);
+        }
       }
     }
     if (e == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -888,13 +933,7 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // ------------------------------------------------------------------ host plan
-struct TcPlan {
-  TcParams tp;
-  CUtensorMap wc, wv, wc_lo, wv_lo;
-  size_t smem;
-  int grid;
-  int form;
-};
+constexpr int kMaxBatch = PV_MAX_BATCH;
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -936,11 +975,17 @@ uint32_t make_idesc(int form, int M, int N) {
 
 size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
-cudaError_t set_smem_attr(int form, int bytes) {
-  if (form == kF16) return cudaFuncSetAttribute(k_blend_tc<kF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+int form_of(int operand_fmt) {
+  return operand_fmt == PV_FMT_F16 ? kF16 : (operand_fmt == PV_FMT_BF16 ? kBF16 : kF32);
+}
+
+template <int MAXV>
+cudaError_t set_smem_attr_v(int form, int bytes) {
+  if (form == kF16)
+    return cudaFuncSetAttribute(k_blend_tc<kF16, MAXV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (form == kBF16)
-    return cudaFuncSetAttribute(k_blend_tc<kBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  return cudaFuncSetAttribute(k_blend_tc<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_blend_tc<kBF16, MAXV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(k_blend_tc<kF32, MAXV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // Clusters of `cluster` CTAs (one CTA per SM) that fit on the GPU at once; 0
@@ -959,9 +1004,9 @@ int max_clusters(int form, int cluster, int smem) {
   cfg.numAttrs = 1;
   int n = 0;
   cudaError_t e;
-  if (form == kF16) e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kF16>, &cfg);
-  else if (form == kBF16) e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kBF16>, &cfg);
-  else e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kF32>, &cfg);
+  if (form == kF16) e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kF16, 1>, &cfg);
+  else if (form == kBF16) e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kBF16, 1>, &cfg);
+  else e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kF32, 1>, &cfg);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -969,55 +1014,29 @@ int max_clusters(int form, int cluster, int smem) {
   return n;
 }
 
-}  // namespace
+struct DevInfo {
+  int sms, smem_max;
+};
 
-bool pv_tc_supported(const pv_desc* d, const char** why) {
-  const int ob = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
-  const int nc = d->color_interior, nv = d->vis_interior;
-  if (nc < 2 || nv < 2) {
-    if (why) *why = "tile interiors below 2x2 (guard-band table holds three copies per texel)";
-    return false;
-  }
-  if ((d->rays_per_probe * ob) % 16 != 0) {
-    if (why) *why = "rays_per_probe * operand bytes must be a multiple of 16 (TMA row pitch)";
-    return false;
-  }
-  if (nc * nc > 2 * MT || nv * nv > 2 * MT) {
-    if (why) *why = "tile interiors too large for the tensor-memory accumulators";
-    return false;
-  }
-  int dev = 0, major = 0, minor = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  cudaGetLastError();
-  if (!(major == 10 && minor == 3)) {
-    if (why) *why = "needs an sm_103 GPU (GB300)";
-    return false;
-  }
-  return true;
+cudaError_t dev_info(DevInfo* d) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return e;
 }
 
-cudaError_t pv_tc_plan_create(pv_volume* v) {
-  cudaError_t e = get_encoder();
-  if (e != cudaSuccess) return e;
-  TcPlan* pl = new TcPlan();
-  memset(pl, 0, sizeof(TcPlan));
-  TcParams& tp = pl->tp;
-  const pv_dev& k = v->k;
-  tp.k = k;
-  const int form = k.operand_fmt == PV_FMT_F16 ? kF16 : (k.operand_fmt == PV_FMT_BF16 ? kBF16 : kF32);
-  pl->form = form;
+// Tile layout, stage ring and epilogue regions for volumes shaped like k, with
+// work items of at most np_want probes (fewer when shared memory demands).
+// Fills every field of tp except items, iters and the volume-dependent ones.
+cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int smem_max, TcParams& tp,
+                        size_t* smem) {
   const int ob = form == kF32 ? 4 : 2;
-  int dev = 0, sms = 0, smem_max = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int sb = v->state_bytes;
-  const int np_max = sb == 2 ? 32 : 16;
+  const int sb = k.state_fmt == PV_FMT_F16 ? 2 : 4;
   const int ROWB = form == kF32 ? row_bytes<kF32>() : row_bytes<kF16>();
+  tp.k = k;
+  tp.cluster = cluster;
   tp.kc = ROWB / ob;
-  tp.nchunks = (k.R + tp.kc - 1) / tp.kc;
   // ray (B) tile rows: d | d^2 (| d^2 lo, 16-bit forms) | R | G | B, 32 each
   tp.nvc = form != kF32 ? 3 * GRP : 2 * GRP;
   tp.crow = tp.nvc;
@@ -1061,35 +1080,11 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
     off += w_b;
   }
   tp.stage_bytes = (int)off;
-  // Clusters of `cluster` CTAs can share each weight chunk (multicast); the
-  // grid is the number of CTAs that can be resident at once, in whole
-  // clusters. Measured on GB300 at 16^3 probes x 256 rays, sharing gains
-  // nothing there (the weight tiles come from L2 and the MMAs, not the loads,
-  // bound the main loop), so one CTA per cluster is the default;
-  // PV_TC_CLUSTER=2|4|8 selects sharing.
-  int cluster = 1;
-  if (const char* env = getenv("PV_TC_CLUSTER")) {
-    const int c = atoi(env);
-    if (c == 1 || c == 2 || c == 4 || c == 8) cluster = c;
-  }
-  e = set_smem_attr(form, smem_max);
-  if (e != cudaSuccess) {
-    delete pl;
-    return e;
-  }
-  int resident = sms;
-  if (cluster > 1) {
-    const int nc = max_clusters(form, cluster, smem_max);
-    if (nc > 0) resident = nc * cluster;
-    else cluster = 1;
-  }
-  tp.cluster = cluster;
-  // probes per work item: one item per resident CTA where possible, fewer
-  // probes when the item's tiles would leave room for less than two stages
+  // probes per work item: np_want, fewer when the item's tiles would leave
+  // room for less than two stages
   const size_t n_rsum = (size_t)(k.Tc + k.Tv) * 4, n_pos = (size_t)(k.Tc + k.Tv) * 2;
   const size_t n_gb = (size_t)(tp.gb_c + tp.gb_v) * 4;
-  int np = (k.P + resident - 1) / resident;
-  np = np < 1 ? 1 : (np > np_max ? np_max : np);
+  int np = np_want;
   int stages = 0;
   size_t epi_state = 0, epi_last = 0;
   for (; np >= 1; --np) {
@@ -1103,16 +1098,9 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
     stages = need < (size_t)smem_max ? (int)(((size_t)smem_max - need) / tp.stage_bytes) : 0;
     if (stages >= 2) break;
   }
-  if (stages < 2) {
-    delete pl;
-    return cudaErrorInvalidConfiguration;
-  }
+  if (stages < 2) return cudaErrorInvalidConfiguration;
   if (stages > 4) stages = 4;
   tp.np = np;
-  tp.items = (k.P + np - 1) / np;
-  const int want = (tp.items + cluster - 1) / cluster * cluster;
-  pl->grid = want < resident ? want : resident;
-  tp.iters = (tp.items + pl->grid - 1) / pl->grid;
   tp.stages = stages;
   tp.w_tx = (uint32_t)((form != kF16 ? 2 : 1) * (tp.vbox + tp.cbox) * ROWB);
   tp.stage_tx = (uint32_t)(4 * np * ROWB) + tp.w_tx;
@@ -1131,23 +1119,149 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   off += 1024;
   tp.off_bar = (int)off;
   off += 1024;
-  pl->smem = off + 1024;                       // slack for aligning the dynamic base
-  // weight tensor maps (fixed for the volume's life)
+  *smem = off + 1024;                          // slack for aligning the dynamic base
+  return cudaSuccess;
+}
+
+// The volume's weight tensor maps (fixed for the volume's life).
+cudaError_t encode_w_maps(const pv_dev& k, int form, const TcParams& tp, BlendVol& bv) {
+  const int ob = form == kF32 ? 4 : 2;
   const size_t wplane = (size_t)(k.tc_pad + k.tv_pad) * k.r_pad;
   const uint8_t* w = (const uint8_t*)k.w_op;
-  e = encode_2d(&pl->wc, k.operand_fmt, w, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.cbox);
+  cudaError_t e = encode_2d(&bv.wc, k.operand_fmt, w, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.cbox);
   if (e == cudaSuccess)
-    e = encode_2d(&pl->wv, k.operand_fmt, w + (size_t)k.tc_pad * k.r_pad * ob, k.r_pad, k.tv_pad,
+    e = encode_2d(&bv.wv, k.operand_fmt, w + (size_t)k.tc_pad * k.r_pad * ob, k.r_pad, k.tv_pad,
                   (uint64_t)k.r_pad * ob, tp.kc, tp.vbox);
   if (e == cudaSuccess && form != kF16) {
-    e = encode_2d(&pl->wc_lo, k.operand_fmt, w + wplane * ob, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob,
-                  tp.kc, tp.cbox);
+    e = encode_2d(&bv.wc_lo, k.operand_fmt, w + wplane * ob, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc,
+                  tp.cbox);
     if (e == cudaSuccess)
-      e = encode_2d(&pl->wv_lo, k.operand_fmt, w + (wplane + (size_t)k.tc_pad * k.r_pad) * ob, k.r_pad,
+      e = encode_2d(&bv.wv_lo, k.operand_fmt, w + (wplane + (size_t)k.tc_pad * k.r_pad) * ob, k.r_pad,
                     k.tv_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.vbox);
   } else {
-    pl->wc_lo = pl->wc;
-    pl->wv_lo = pl->wv;
+    bv.wc_lo = bv.wc;
+    bv.wv_lo = bv.wv;
+  }
+  return e;
+}
+
+// Tensor maps of one frame's rays (radiance [3][P][R], dist [P][R]).
+cudaError_t encode_ray_maps(const pv_dev& k, int form, const TcParams& tp, const void* rad, const void* dist,
+                            BlendVol& bv) {
+  const int ob = form == kF32 ? 4 : 2;
+  cudaError_t e = encode_2d(&bv.rad, k.operand_fmt, rad, k.R, (uint64_t)3 * k.P, (uint64_t)k.R * ob, tp.kc, tp.np);
+  if (e == cudaSuccess) e = encode_2d(&bv.dist, k.operand_fmt, dist, k.R, k.P, (uint64_t)k.R * ob, tp.kc, tp.np);
+  return e;
+}
+
+template <int MAXV>
+cudaError_t launch_blend(const BlendArgs<MAXV>& a, int form, int grid, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.tp.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (form == kF16) e = cudaLaunchKernelEx(&cfg, k_blend_tc<kF16, MAXV>, a);
+  else if (form == kBF16) e = cudaLaunchKernelEx(&cfg, k_blend_tc<kBF16, MAXV>, a);
+  else e = cudaLaunchKernelEx(&cfg, k_blend_tc<kF32, MAXV>, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+struct TcPlan {
+  BlendArgs<1> args;
+  size_t smem;
+  int grid;
+  int form;
+};
+
+}  // namespace
+
+// Batch plan (opaque to the API layer).
+struct pv_tc_batch {
+  BlendArgs<kMaxBatch> args;
+  size_t smem;
+  int grid;
+  int form;
+  int n;
+  pv_volume* vols[kMaxBatch];
+};
+
+bool pv_tc_supported(const pv_desc* d, const char** why) {
+  const int ob = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
+  const int nc = d->color_interior, nv = d->vis_interior;
+  if (nc < 2 || nv < 2) {
+    if (why) *why = "tile interiors below 2x2 (guard-band table holds three copies per texel)";
+    return false;
+  }
+  if ((d->rays_per_probe * ob) % 16 != 0) {
+    if (why) *why = "rays_per_probe * operand bytes must be a multiple of 16 (TMA row pitch)";
+    return false;
+  }
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaGetLastError();
+  if (!(major == 10 && minor == 3)) {
+    if (why) *why = "needs an sm_103 GPU (GB300)";
+    return false;
+  }
+  return true;
+}
+
+cudaError_t pv_tc_plan_create(pv_volume* v) {
+  cudaError_t e = get_encoder();
+  DevInfo di;
+  if (e == cudaSuccess) e = dev_info(&di);
+  if (e != cudaSuccess) return e;
+  const pv_dev& k = v->k;
+  const int form = form_of(k.operand_fmt);
+  e = set_smem_attr_v<1>(form, di.smem_max);
+  if (e != cudaSuccess) return e;
+  // Clusters of `cluster` CTAs can share each weight chunk (multicast); the
+  // grid is the number of CTAs that can be resident at once, in whole
+  // clusters. Measured on GB300 at 16^3 probes x 256 rays, sharing gains
+  // nothing there (the MMAs, not the weight loads, bound the main loop), so
+  // one CTA per cluster is the default; PV_TC_CLUSTER=2|4|8 selects sharing.
+  int cluster = 1;
+  if (const char* env = getenv("PV_TC_CLUSTER")) {
+    const int c = atoi(env);
+    if (c == 1 || c == 2 || c == 4 || c == 8) cluster = c;
+  }
+  int resident = di.sms;
+  if (cluster > 1) {
+    const int nc = max_clusters(form, cluster, di.smem_max);
+    if (nc > 0) resident = nc * cluster;
+    else cluster = 1;
+  }
+  // one item per resident CTA where possible
+  const int np_max = v->state_bytes == 2 ? 32 : 16;
+  int np = (k.P + resident - 1) / resident;
+  np = np < 1 ? 1 : (np > np_max ? np_max : np);
+  TcPlan* pl = new TcPlan();
+  memset(pl, 0, sizeof(TcPlan));
+  TcParams& tp = pl->args.tp;
+  e = make_layout(k, form, np, cluster, di.smem_max, tp, &pl->smem);
+  if (e == cudaSuccess) {
+    tp.items = (k.P + tp.np - 1) / tp.np;
+    const int want = (tp.items + cluster - 1) / cluster * cluster;
+    pl->grid = want < resident ? want : resident;
+    tp.iters = (tp.items + pl->grid - 1) / pl->grid;
+    pl->form = form;
+    pl->args.nvol = 1;
+    BlendVol& bv = pl->args.v[0];
+    bv.k = k;
+    bv.item0 = 0;
+    bv.nchunks = (k.R + tp.kc - 1) / tp.kc;
+    e = encode_w_maps(k, form, tp, bv);
   }
   if (e != cudaSuccess) {
     delete pl;
@@ -1167,38 +1281,74 @@ void pv_tc_plan_destroy(pv_volume* v) {
 cudaError_t pv_launch_blend_tc(pv_volume* v, const void* rad, const void* dist, cudaStream_t st) {
   TcPlan* pl = (TcPlan*)v->tc_plan;
   if (!pl) return cudaErrorNotSupported;
-  const pv_dev& k = v->k;
-  const int ob = pl->form == kF32 ? 4 : 2;
-  CUtensorMap mr, md;
-  cudaError_t e = encode_2d(&mr, k.operand_fmt, rad, k.R, (uint64_t)3 * k.P, (uint64_t)k.R * ob,
-                            pl->tp.kc, pl->tp.np);
-  if (e == cudaSuccess)
-    e = encode_2d(&md, k.operand_fmt, dist, k.R, k.P, (uint64_t)k.R * ob, pl->tp.kc, pl->tp.np);
+  BlendArgs<1> a = pl->args;
+  a.tp.k = v->k;
+  a.v[0].k = v->k;
+  cudaError_t e = encode_ray_maps(v->k, pl->form, a.tp, rad, dist, a.v[0]);
   if (e != cudaSuccess) return e;
-  TcParams tp = pl->tp;
-  tp.k = k;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = tp.cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(pl->grid);
-  cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = pl->smem;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  switch (pl->form) {
-    case kF16:
-      e = cudaLaunchKernelEx(&cfg, k_blend_tc<kF16>, tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
-      break;
-    case kBF16:
-      e = cudaLaunchKernelEx(&cfg, k_blend_tc<kBF16>, tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
-      break;
-    default:
-      e = cudaLaunchKernelEx(&cfg, k_blend_tc<kF32>, tp, mr, md, pl->wc, pl->wv, pl->wc_lo, pl->wv_lo);
-      break;
+  return launch_blend(a, pl->form, pl->grid, pl->smem, st);
+}
+
+cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc_batch** out) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  cudaError_t e = get_encoder();
+  DevInfo di;
+  if (e == cudaSuccess) e = dev_info(&di);
+  if (e != cudaSuccess) return e;
+  const pv_dev& k0 = vols[0]->k;
+  const int form = form_of(k0.operand_fmt);
+  e = set_smem_attr_v<kMaxBatch>(form, di.smem_max);
+  if (e != cudaSuccess) return e;
+  int total = 0;
+  for (int i = 0; i < n; ++i) total += vols[i]->k.P;
+  const int np_max = vols[0]->state_bytes == 2 ? 32 : 16;
+  int np = np_want > 0 ? np_want : (total + di.sms - 1) / di.sms;
+  np = np < 1 ? 1 : (np > np_max ? np_max : np);
+  pv_tc_batch* b = new pv_tc_batch();
+  memset(b, 0, sizeof(pv_tc_batch));
+  TcParams& tp = b->args.tp;
+  e = make_layout(k0, form, np, 1, di.smem_max, tp, &b->smem);
+  if (e == cudaSuccess) {
+    int items = 0;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      const pv_dev& k = vols[i]->k;
+      BlendVol& bv = b->args.v[i];
+      bv.k = k;
+      bv.item0 = items;
+      bv.nchunks = (k.R + tp.kc - 1) / tp.kc;
+      items += (k.P + tp.np - 1) / tp.np;
+      e = encode_w_maps(k, form, tp, bv);
+      b->vols[i] = vols[i];
+    }
+    tp.items = items;
+    b->grid = items < di.sms ? items : di.sms;
+    tp.iters = (items + b->grid - 1) / b->grid;
+    b->args.nvol = n;
+    b->form = form;
+    b->n = n;
   }
-  return e != cudaSuccess ? e : cudaGetLastError();
+  if (e != cudaSuccess) {
+    delete b;
+    return e;
+  }
+  *out = b;
+  return cudaSuccess;
+}
+
+void pv_tc_batch_destroy(pv_tc_batch* b) { delete b; }
+
+int pv_tc_batch_np(const pv_tc_batch* b) { return b->args.tp.np; }
+
+cudaError_t pv_tc_batch_launch(pv_tc_batch* b, const void* const* rad, const void* const* dist, cudaStream_t st) {
+  // the launch arguments live on the host stack for the duration of the call
+  BlendArgs<kMaxBatch>* a = new BlendArgs<kMaxBatch>(b->args);
+  cudaError_t e = cudaSuccess;
+  a->tp.k = b->vols[0]->k;
+  for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+    a->v[i].k = b->vols[i]->k;
+    e = encode_ray_maps(b->vols[i]->k, b->form, a->tp, rad[i], dist[i], a->v[i]);
+  }
+  if (e == cudaSuccess) e = launch_blend(*a, b->form, b->grid, b->smem, st);
+  delete a;
+  return e;
 }

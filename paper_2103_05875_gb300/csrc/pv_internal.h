@@ -72,6 +72,10 @@ cudaError_t pv_simt_prepare();
 cudaError_t pv_launch_blend_simt(const pv_dev& k, const void* rad, const void* dist,
                                  cudaStream_t s);
 cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t s);
+// batched forms (blockIdx.y = volume; n <= PV_MAX_BATCH)
+cudaError_t pv_launch_weights_batch(const pv_dev* ks, const float* const* dirs, int n, int want_rt, int want_op,
+                                    cudaStream_t s);
+cudaError_t pv_launch_select_pack_batch(const pv_dev* ks, int n, cudaStream_t s);
 cudaError_t pv_launch_recompute_flags(const pv_dev& k, cudaStream_t s);
 
 // tensor-core blend (pv_blend_tc.cu)
@@ -79,6 +83,12 @@ bool pv_tc_supported(const pv_desc* d, const char** why);
 cudaError_t pv_tc_plan_create(pv_volume* v);
 void pv_tc_plan_destroy(pv_volume* v);
 cudaError_t pv_launch_blend_tc(pv_volume* v, const void* rad, const void* dist, cudaStream_t s);
+// one persistent launch over the work items of several volumes of equal shapes
+struct pv_tc_batch;
+cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc_batch** out);
+void pv_tc_batch_destroy(pv_tc_batch* b);
+int pv_tc_batch_np(const pv_tc_batch* b);
+cudaError_t pv_tc_batch_launch(pv_tc_batch* b, const void* const* rad, const void* const* dist, cudaStream_t s);
 
 // error reporting (pv_api.cpp)
 pv_status pv_set_error(pv_status s, const char* fmt, ...);

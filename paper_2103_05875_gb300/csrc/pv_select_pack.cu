@@ -129,7 +129,9 @@ __device__ __forceinline__ void block_reduce3(int& a, int& b, int& c, int* sh) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range) {
+// Block `bid` of the `nblocks` blocks that select and pack volume k, each
+// block owning `range` consecutive probes.
+__device__ __forceinline__ void select_pack_block(const pv_dev& k, int range, int bid, int nblocks) {
   __shared__ SpTables tb;
   __shared__ int red[3 * SP_WARPS];
   __shared__ int slot_c[SP_MAX_RANGE], slot_v[SP_MAX_RANGE];
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range)
   const uint32_t seq = k.sel[0];
   const uint32_t par = seq & 1u;
   const int prev_cnt_c = (int)k.sel[2 + 2 * (par ^ 1u)], prev_cnt_v = (int)k.sel[3 + 2 * (par ^ 1u)];
-  const int pb = blockIdx.x * range, pe = min(k.P, pb + range);
+  const int pb = bid * range, pe = min(k.P, pb + range);
   const int W = k.chg_words, wb = pb >> 5;
 
   for (int q = tid; q < 3 * k.Tc; q += SP_THREADS) {
@@ -214,12 +216,12 @@ __global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range)
     }
   }
   // 4. clear slots used by the previous frame and empty now
-  for (int s = tot_c + blockIdx.x * SP_WARPS + wid; s < prev_cnt_c; s += gridDim.x * SP_WARPS)
+  for (int s = tot_c + bid * SP_WARPS + wid; s < prev_cnt_c; s += nblocks * SP_WARPS)
     pack_color_probe(k, tb, -1, s, lane);
-  for (int s = tot_v + blockIdx.x * SP_WARPS + wid; s < prev_cnt_v; s += gridDim.x * SP_WARPS)
+  for (int s = tot_v + bid * SP_WARPS + wid; s < prev_cnt_v; s += nblocks * SP_WARPS)
     pack_vis_probe(k, tb, -1, s, lane);
   // 5. counts, and the select sequence once every block is done
-  if (blockIdx.x == 0 && tid == 0) {
+  if (bid == 0 && tid == 0) {
     k.counts[0] = (uint32_t)tot_c;
     k.counts[1] = (uint32_t)tot_v;
     k.sel[2 + 2 * par] = (uint32_t)tot_c;
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range)
   if (tid == 0) {
     __threadfence();
     const uint32_t ticket = atomicAdd(&k.sel[1], 1u);
-    if (ticket == gridDim.x - 1) {
+    if (ticket == (uint32_t)nblocks - 1) {
       k.sel[1] = 0;
       k.sel[0] = seq + 1u;
       *k.sel_frame = *k.frame;
@@ -238,18 +240,60 @@ __global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range)
   }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range) {
+  select_pack_block(k, range, blockIdx.x, gridDim.x);
+}
 
-cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t st) {
+// Several volumes in one launch: blockIdx.y is the volume.
+struct SpBatch {
+  pv_dev k[PV_MAX_BATCH];
+  int range[PV_MAX_BATCH];
+  int nblocks[PV_MAX_BATCH];
+};
+
+__global__ void __launch_bounds__(SP_THREADS) k_select_pack_batch(const __grid_constant__ SpBatch b) {
+  const int v = blockIdx.y;
+  if ((int)blockIdx.x >= b.nblocks[v]) return;
+  select_pack_block(b.k[v], b.range[v], blockIdx.x, b.nblocks[v]);
+}
+
+// One probe per warp keeps every probe's loads in flight at once (a warp
+// waits one memory round trip per probe); larger volumes take several.
+int sp_range(const pv_dev& k, int sms) {
+  int range = SP_WARPS;
+  while ((k.P + range - 1) / range > 16 * sms && range < SP_MAX_RANGE) range *= 2;
+  return range;
+}
+
+int device_sms() {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // one probe per warp keeps every probe's loads in flight at once (a warp
-  // waits one memory round trip per probe); larger volumes take several
-  int range = SP_WARPS;
-  while ((k.P + range - 1) / range > 16 * sms && range < SP_MAX_RANGE) range *= 2;
+  return sms;
+}
+
+}  // namespace
+
+cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t st) {
+  const int range = sp_range(k, device_sms());
   const int blocks = (k.P + range - 1) / range;
   k_select_pack<<<blocks, SP_THREADS, 0, st>>>(k, range);
+  return cudaGetLastError();
+}
+
+cudaError_t pv_launch_select_pack_batch(const pv_dev* ks, int n, cudaStream_t st) {
+  if (n < 1 || n > PV_MAX_BATCH) return cudaErrorInvalidValue;
+  SpBatch* b = new SpBatch();
+  const int sms = device_sms();
+  int most = 0;
+  for (int i = 0; i < n; ++i) {
+    b->k[i] = ks[i];
+    b->range[i] = sp_range(ks[i], sms);
+    b->nblocks[i] = (ks[i].P + b->range[i] - 1) / b->range[i];
+    most = b->nblocks[i] > most ? b->nblocks[i] : most;
+  }
+  k_select_pack_batch<<<dim3(most, n), SP_THREADS, 0, st>>>(*b);
+  delete b;
   return cudaGetLastError();
 }
 

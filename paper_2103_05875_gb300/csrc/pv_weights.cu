@@ -72,10 +72,11 @@ __device__ __forceinline__ void store_plane(void* base, size_t i, float w, int f
   else reinterpret_cast<float*>(base)[i] = w;
 }
 
-__global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restrict__ dirs,
-                                                 int want_rt, int want_op) {
+// Weights of texel tg (colour texels first) of volume k; one block of 256
+// threads.
+__device__ __forceinline__ void weights_block(const pv_dev& k, const float* __restrict__ dirs, int want_rt,
+                                              int want_op, int tg, bool first_block) {
   const int T = k.Tc + k.Tv;
-  const int tg = blockIdx.x;
   const bool vis = tg >= k.Tc;
   const int n = vis ? k.nv : k.nc;
   const int t = vis ? tg - k.Tc : tg;
@@ -136,17 +137,50 @@ __global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restri
   }
   if (threadIdx.x == 0) k.sums[tg] = red[0];
 
-  if (blockIdx.x == 0) {            // this frame's changed-probe bits start cleared
+  if (first_block) {                // this frame's changed-probe bits start cleared
     for (int w = threadIdx.x; w < 2 * k.chg_words; w += blockDim.x) k.chg[w] = 0u;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (first_block && threadIdx.x == 0) {
     unsigned long long f = *k.frame;
     *k.hy = (f == 0ull && k.first_frame_no_hysteresis) ? 0.0f : k.h;
     *k.frame = f + 1ull;
   }
 }
 
+__global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restrict__ dirs,
+                                                 int want_rt, int want_op) {
+  weights_block(k, dirs, want_rt, want_op, blockIdx.x, blockIdx.x == 0);
+}
+
+// Several volumes in one launch: blockIdx.y is the volume.
+struct WeightsBatch {
+  pv_dev k[PV_MAX_BATCH];
+  const float* dirs[PV_MAX_BATCH];
+};
+
+__global__ void __launch_bounds__(256) k_weights_batch(const __grid_constant__ WeightsBatch b, int want_rt,
+                                                       int want_op) {
+  const pv_dev& k = b.k[blockIdx.y];
+  if ((int)blockIdx.x >= k.Tc + k.Tv) return;
+  weights_block(k, b.dirs[blockIdx.y], want_rt, want_op, blockIdx.x, blockIdx.x == 0);
+}
+
 }  // namespace
+
+cudaError_t pv_launch_weights_batch(const pv_dev* ks, const float* const* dirs, int n, int want_rt, int want_op,
+                                    cudaStream_t st) {
+  if (n < 1 || n > PV_MAX_BATCH) return cudaErrorInvalidValue;
+  WeightsBatch* b = new WeightsBatch();
+  int most = 0;
+  for (int i = 0; i < n; ++i) {
+    b->k[i] = ks[i];
+    b->dirs[i] = dirs[i];
+    most = ks[i].Tc + ks[i].Tv > most ? ks[i].Tc + ks[i].Tv : most;
+  }
+  k_weights_batch<<<dim3(most, n), 256, 0, st>>>(*b, want_rt, want_op);
+  delete b;
+  return cudaGetLastError();
+}
 
 cudaError_t pv_launch_weights(const pv_dev& k, const float* dirs, int want_rt, int want_op,
                               cudaStream_t st) {
