@@ -295,6 +295,58 @@ pv_status probe_batch_select_and_pack(pv_batch* batch, pv_frame* out, void* stre
 pv_status probe_batch_tune(pv_batch* batch, const void* const* radiance, const void* const* dist,
                            const float* const* dirs, int32_t reps, int32_t* out_probes_per_item, void* stream);
 
+/* ----------------------------------------------------------------- server */
+/*
+ * Served form: a request loop for many clients, each owning one probe volume
+ * (a session). A session is admitted while its volume's device bytes fit the
+ * memory budget and a slot is free; otherwise it waits, and waiting sessions
+ * are admitted in arrival order as closing sessions free memory and slots.
+ * Admitted volumes stay resident on the device. Per tick (e.g. 60 Hz), the
+ * clients that submitted rays are updated together: volumes of equal shapes
+ * and formats go into batches of at most max_batch (the batched form above),
+ * so every client of a tick shares the same launches. Results equal those of
+ * the same client served alone.
+ *  pv_server_open    open session `client` for a volume `desc` (its kernel
+ *                    field is ignored: the tensor-core blend is used).
+ *                    PV_OK admitted, PV_PENDING waiting, PV_ERR_OOM the volume
+ *                    alone exceeds the budget, PV_ERR_INVALID id in use.
+ *  pv_server_close   end a session (waits for launched ticks), then admit
+ *                    waiting sessions that fit.
+ *  pv_server_status  admitted: 1, 0 waiting, -1 unknown client, -2 its volume
+ *                    could not be created at admission (close the session);
+ *                    used bytes; number of waiting sessions (outputs may be
+ *                    NULL).
+ *  pv_server_volume  the admitted client's volume (owned by the server, valid
+ *                    until the session closes), e.g. to export its state.
+ *  pv_submit         rays of an admitted client for the next tick (device
+ *                    pointers, layouts as for probe_update, kept alive and
+ *                    unchanged until the ticket completes); one submission
+ *                    per client per tick. PV_ERR_BUSY: not admitted yet, or
+ *                    already submitted for this tick.
+ *  pv_server_tick    launch this tick's work on `stream` (asynchronous).
+ *  pv_poll           PV_PENDING until the ticket's tick has completed on the
+ *                    device, then PV_OK and the client's packed frame (device
+ *                    pointers valid until the client's next tick is launched;
+ *                    count_c / count_v are -1: read count_*_dev).
+ */
+typedef struct pv_server_desc {
+  uint64_t mem_budget_bytes;    /* device bytes the admitted volumes may hold */
+  int32_t max_slots;            /* sessions admitted at once */
+  int32_t max_batch;            /* volumes per batched launch, 1..PV_MAX_BATCH */
+} pv_server_desc;
+typedef struct pv_server pv_server;
+pv_status pv_server_create(const pv_server_desc* desc, pv_server** out);
+pv_status pv_server_destroy(pv_server* server);
+pv_status pv_server_open(pv_server* server, int32_t client, const pv_desc* desc);
+pv_status pv_server_close(pv_server* server, int32_t client);
+pv_status pv_server_status(pv_server* server, int32_t client, int32_t* admitted, uint64_t* used_bytes,
+                           int32_t* waiting);
+pv_status pv_server_volume(pv_server* server, int32_t client, pv_volume** out);
+pv_status pv_submit(pv_server* server, int32_t client, const void* radiance, const void* dist,
+                    const float* dirs, uint64_t* ticket);
+pv_status pv_server_tick(pv_server* server, void* stream, uint64_t* tick);
+pv_status pv_poll(pv_server* server, uint64_t ticket, pv_frame* out);
+
 #ifdef __cplusplus
 }
 #endif

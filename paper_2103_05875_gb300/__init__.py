@@ -61,6 +61,10 @@ class pv_frame(C.Structure):
                 ("count_c", C.c_int64), ("count_v", C.c_int64), ("frame", C.c_uint64)]
 
 
+class pv_server_desc(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_slots", C.c_int32), ("max_batch", C.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libprobestream.so is not built ({LIB_PATH}); run "
@@ -91,6 +95,15 @@ def _load():
         "probe_batch_update": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]),
         "probe_batch_select_and_pack": (i32, [vp, C.POINTER(pv_frame), vp]),
         "probe_batch_tune": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(i32), vp]),
+        "pv_server_create": (i32, [C.POINTER(pv_server_desc), C.POINTER(vp)]),
+        "pv_server_destroy": (i32, [vp]),
+        "pv_server_open": (i32, [vp, i32, C.POINTER(pv_desc)]),
+        "pv_server_close": (i32, [vp, i32]),
+        "pv_server_status": (i32, [vp, i32, C.POINTER(i32), C.POINTER(u64), C.POINTER(i32)]),
+        "pv_server_volume": (i32, [vp, i32, C.POINTER(vp)]),
+        "pv_submit": (i32, [vp, i32, vp, vp, vp, C.POINTER(u64)]),
+        "pv_server_tick": (i32, [vp, vp, C.POINTER(u64)]),
+        "pv_poll": (i32, [vp, u64, C.POINTER(pv_frame)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -298,9 +311,10 @@ def device_view(ptr: int, shape, dtype, strides_bytes=None):
 class ProbeVolume:
     """A probe volume on the current CUDA device (see probe_volume_create)."""
 
-    def __init__(self, spec=None, **kw):
+    def __init__(self, spec=None, _handle=None, **kw):
         self.desc = make_desc(spec, **kw)
-        self.handle = probe_volume_create(self.desc)
+        self._owned = _handle is None
+        self.handle = probe_volume_create(self.desc) if _handle is None else _handle
         self.info = probe_volume_info(self.handle)
         self.P = self.info.probes
         self.R = self.info.rays
@@ -310,7 +324,8 @@ class ProbeVolume:
 
     def close(self):
         if getattr(self, "handle", None):
-            probe_volume_destroy(self.handle)
+            if self._owned:
+                probe_volume_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -398,3 +413,78 @@ class ProbeBatch:
 
     def tune(self, radiance, dist, dirs, reps: int = 3, stream=None) -> int:
         return probe_batch_tune(self.handle, radiance, dist, dirs, reps, stream)
+
+
+PV_PENDING_STATUS = 1
+
+
+def _desc_kwargs(d: pv_desc) -> dict:
+    inv_fmt = {v: k for k, v in FMT.items()}
+    inv_code = {v: k for k, v in CODE.items()}
+    return dict(nx=d.nx, ny=d.ny, nz=d.nz, rays=d.rays_per_probe, color_interior=d.color_interior,
+                vis_interior=d.vis_interior, hysteresis=d.hysteresis, sharpness=d.sharpness,
+                state_fmt=inv_fmt[d.state_fmt], operand_fmt=inv_fmt[d.operand_fmt],
+                color_code=inv_code[d.color_code], color_lsb=bool(d.color_lsb),
+                first_frame_no_hysteresis=bool(d.first_frame_no_hysteresis))
+
+
+class ProbeServer:
+    """The served form (pv_server_*): sessions admitted by device memory and slots, batched
+    per tick. open() returns True when admitted, False while waiting."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int, max_batch: int = 16):
+        d = pv_server_desc(int(mem_budget_bytes), int(max_slots), int(max_batch))
+        h = C.c_void_p()
+        _check(lib.pv_server_create(C.byref(d), C.byref(h)), "pv_server_create")
+        self.handle = h.value
+        self.descs = {}
+
+    def close_server(self):
+        if getattr(self, "handle", None):
+            _check(lib.pv_server_destroy(self.handle), "pv_server_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close_server()
+        except Exception:
+            pass
+
+    def open(self, client: int, spec=None, **kw) -> bool:
+        d = make_desc(spec, **kw)
+        st = _check(lib.pv_server_open(self.handle, int(client), C.byref(d)), "pv_server_open")
+        self.descs[client] = d
+        return st == 0
+
+    def close(self, client: int):
+        _check(lib.pv_server_close(self.handle, int(client)), "pv_server_close")
+        self.descs.pop(client, None)
+
+    def status(self, client: int = -1):
+        a, used, w = C.c_int32(), C.c_uint64(), C.c_int32()
+        _check(lib.pv_server_status(self.handle, int(client), C.byref(a), C.byref(used), C.byref(w)),
+               "pv_server_status")
+        return a.value, used.value, w.value
+
+    def submit(self, client: int, radiance, dist, dirs) -> int:
+        t = C.c_uint64()
+        _check(lib.pv_submit(self.handle, int(client), _ptr(radiance), _ptr(dist), _ptr(dirs), C.byref(t)),
+               "pv_submit")
+        return t.value
+
+    def tick(self, stream=None) -> int:
+        t = C.c_uint64()
+        _check(lib.pv_server_tick(self.handle, _stream(stream), C.byref(t)), "pv_server_tick")
+        return t.value
+
+    def volume(self, client: int) -> "ProbeVolume":
+        """A view of the admitted client's volume (owned by the server)."""
+        h = C.c_void_p()
+        _check(lib.pv_server_volume(self.handle, int(client), C.byref(h)), "pv_server_volume")
+        return ProbeVolume(None, _handle=h.value, **_desc_kwargs(self.descs[client]))
+
+    def poll(self, ticket: int):
+        """None while pending, else the client's pv_frame."""
+        fr = pv_frame()
+        st = _check(lib.pv_poll(self.handle, int(ticket), C.byref(fr)), "pv_poll")
+        return None if st == PV_PENDING_STATUS else fr
