@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--forms", default="f32,f16,bf16")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -267,6 +270,183 @@ def time_e2e(spec, steps, seed):
             "d2h_bytes_per_step": int(bo_fixed + idx_bytes / steps), "ms_per_step": ms / steps}
 
 
+def _graph_steps(step_fns, steps, warmup):
+    """Captures each step function as a CUDA graph, replays warm-up then timed steps; ms."""
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for f in step_fns:
+            f()
+    torch.cuda.synchronize()
+    graphs = []
+    for f in step_fns:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            f()
+        graphs.append(g)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(warmup):
+            graphs[s % len(graphs)].replay()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t0.record()
+        for s in range(steps):
+            graphs[s % len(graphs)].replay()
+        t1.record()
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1)
+
+
+def time_batched(steps, warmup, seed, operand_fmt="f32"):
+    """Batched form: the 12 uneven volumes of the batched workload, one step = batched weights +
+    one persistent blend launch + batched select/pack, under CUDA graphs; against the same
+    volumes updated one by one (plain path, 2 launches + 1 per volume each)."""
+    import torch
+    import paper_2103_05875_gb300 as pv
+    import pv_workload as wl
+    specs = wl.config4(operand_fmt)
+    P = sum(s.probes for s in specs)
+    frames = []
+    for f in range(2):
+        ins = []
+        for i, spec in enumerate(specs):
+            fs = wl.FrameStream(spec, seed, volume=i, mode="noisy")
+            ins.append((wl.to_operand(fs.radiance(f), operand_fmt).cuda(),
+                        wl.to_operand(fs.dist(f), operand_fmt).cuda(),
+                        torch.from_numpy(fs.directions(f)).cuda()))
+        frames.append(ins)
+    vols = [pv.ProbeVolume(s) for s in specs]
+    batch = pv.ProbeBatch(vols)
+    np_auto = batch.probes_per_item
+    args0 = ([x[0] for x in frames[0]], [x[1] for x in frames[0]], [x[2] for x in frames[0]])
+    np_tuned = batch.tune(*args0, reps=3)
+
+    def bstep(f):
+        def run():
+            ins = frames[f]
+            batch.update([x[0] for x in ins], [x[1] for x in ins], [x[2] for x in ins])
+            batch.select_and_pack()
+        return run
+    ms_b = _graph_steps([bstep(0), bstep(1)], steps, warmup)
+    singles = [pv.ProbeVolume(s) for s in specs]
+
+    def sstep(f):
+        def run():
+            for v, (r, d, q) in zip(singles, frames[f]):
+                v.update(r, d, q)
+                v.select_and_pack()
+        return run
+    ms_s = _graph_steps([sstep(0), sstep(1)], steps, warmup)
+    out = {"workload": "12 volumes 8x4x8 .. 32x8x32 (37,376 probes), rays 128/192/256, FP16 state, "
+                       f"{operand_fmt} operands, noisy", "probes_per_step": P,
+           "value": P * steps / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / steps,
+           "probes_per_item": {"default": np_auto, "tuned": np_tuned},
+           "launches_per_step": 3,
+           "volume_by_volume": {"value": P * steps / (ms_s / 1e3), "ms_per_step": ms_s / steps,
+                                "launches_per_step": 3 * len(specs)}}
+    batch.close()
+    for v in vols + singles:
+        v.close()
+    del frames
+    torch.cuda.empty_cache()
+    return out
+
+
+def _served_run(arrivals, inputs, ticks, budget, slots, serial):
+    """One pass of the 60 Hz request loop; returns (probes served, tick latencies in ms, waits)."""
+    import torch
+    import paper_2103_05875_gb300 as pv
+    server = None if serial else pv.ProbeServer(budget, slots)
+    singles = {}
+    active, waiting_seen = {}, 0
+    probes, lat = 0, []
+    for t in range(ticks):
+        now = t / 60.0
+        for a in arrivals:                                  # arrivals of this tick
+            if now - 1 / 60.0 < a.arrive_s <= now:
+                if serial:
+                    singles[a.client] = pv.ProbeVolume(a.spec)
+                    active[a.client] = a
+                else:
+                    if not server.open(a.client, a.spec):
+                        waiting_seen += 1
+                    active[a.client] = a
+        for c, a in list(active.items()):                   # sessions that ended
+            if now > a.arrive_s + a.session_s:
+                if serial:
+                    singles.pop(c).close()
+                else:
+                    server.close(c)
+                del active[c]
+        t0 = time.perf_counter()
+        served = []
+        if serial:
+            for c, a in active.items():
+                r, d, q = inputs[(a.spec.nx, a.spec.ny, a.spec.nz, a.spec.rays)][t % 2]
+                singles[c].update(r, d, q)
+                singles[c].select_and_pack()
+                served.append(a.spec.probes)
+            torch.cuda.synchronize()
+        else:
+            tickets = []
+            for c, a in active.items():
+                if server.status(c)[0] != 1:
+                    continue
+                r, d, q = inputs[(a.spec.nx, a.spec.ny, a.spec.nz, a.spec.rays)][t % 2]
+                tickets.append(server.submit(c, r, d, q))
+                served.append(a.spec.probes)
+            server.tick()
+            for tk in tickets:
+                while server.poll(tk) is None:
+                    pass
+        if served:
+            lat.append((time.perf_counter() - t0) * 1e3)
+            probes += sum(served)
+    for v in singles.values():
+        v.close()
+    if server is not None:
+        server.close_server()
+    return probes, lat, waiting_seen
+
+
+def time_served(seconds, seed):
+    """Served form: 64 clients arriving Poisson(4/s) with exponential sessions (mean 8 s), each
+    owning a volume of the batched workload's sizes; 60 Hz ticks over `seconds` of simulated
+    time, run back to back; per-tick latency from the first submission to the last completed
+    poll (through the public API, host loop included). Against the same schedule served by
+    plain per-client updates."""
+    import torch
+    import pv_workload as wl
+    arrivals = wl.served_clients(64, 4.0, 8.0, seed=seed)
+    shapes = {}
+    for a in arrivals:
+        key = (a.spec.nx, a.spec.ny, a.spec.nz, a.spec.rays)
+        if key not in shapes:
+            fs = wl.FrameStream(a.spec, seed, volume=len(shapes), mode="noisy")
+            shapes[key] = [(wl.to_operand(fs.radiance(f), a.spec.operand_fmt).cuda(),
+                            wl.to_operand(fs.dist(f), a.spec.operand_fmt).cuda(),
+                            torch.from_numpy(fs.directions(f)).cuda()) for f in range(2)]
+    ticks = int(seconds * 60)
+
+    def summarise(probes, lat, waits):
+        total_s = sum(lat) / 1e3
+        q = sorted(lat)
+        return {"value": probes / total_s if total_s else 0.0, "unit": UNIT,
+                "p50_ms": q[len(q) // 2] if q else None, "p99_ms": q[min(len(q) - 1, int(0.99 * len(q)))] if q else None,
+                "ticks": len(lat), "client_updates_probes": probes, "admission_waits": waits}
+    res = {"workload": f"64 clients, Poisson 4/s arrivals, exp(8 s) sessions, batched-workload sizes, "
+                       f"60 Hz ticks, {seconds:g} s simulated, 40 GB budget"}
+    res.update(summarise(*_served_run(arrivals, shapes, ticks, 40 << 30, 64, serial=False)))
+    res["serial_plain"] = summarise(*_served_run(arrivals, shapes, ticks, 40 << 30, 64, serial=True))
+    tight = summarise(*_served_run(arrivals, shapes, ticks, 256 << 20, 16, serial=False))
+    res["tight_budget_256MB_16_slots"] = tight
+    del shapes
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline(spec, seed, budget_s=12.0, max_frames=40):
     """The FP64 oracle as it stands, on a bounded number of frames of the same workload."""
     import numpy as np
@@ -369,6 +549,10 @@ def run_ours(args, ws, rank, local):
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": alg},
         "clocks": clk,
     }
+    if not args.no_batched:
+        line["batched"] = time_batched(max(10, args.steps // 2), args.warmup, seed)
+    if rank == 0 and not args.no_served:
+        line["served"] = time_served(args.served_seconds, seed)
     if rank == 0 and ws == 1 and not args.no_e2e:
         line["e2e"] = time_e2e(wl.config2(operand_fmt=forms[0]), max(10, args.steps // 2), seed)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
