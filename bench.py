@@ -32,6 +32,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 NBUF = 8
+# DRAM bytes (read + write) of one k_blend_tc launch of the FP32 form from one ncu capture
+# (profiles/blend_tc_16x16x16_256rays.md), valid only for the kernel source it was taken
+# on: reported as null once the source has changed.
+BLEND_TRAFFIC = {"source_sha256_prefix": "f1ea0ca096a3375e", "f32": 27566592 + 512}
 METRIC = "probes updated+packed/sec at 16^3 probes x 256 rays (plain FP32 form)"
 UNIT = "probes/s"
 WORKLOAD = "16x16x16 probes, 256 rays/probe, colour 6x6+1, vis 14x14+1, FP16 state, h=0.97, s=50"
@@ -531,6 +535,10 @@ def run_ours(args, ws, rank, local):
     bpp = blend_bytes_per_probe(256, op_bytes)
     alg = bpp * P + (36 + 196) * 256 * 4
     achieved = alg / (head["blend_ms"] / 1e3) / 1e9
+    import hashlib
+    src = os.path.join(ROOT, "paper_2103_05875_gb300", "csrc", "pv_blend_tc.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    traffic = BLEND_TRAFFIC.get(forms[0]) if sha == BLEND_TRAFFIC["source_sha256_prefix"] else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -545,7 +553,7 @@ def run_ours(args, ws, rank, local):
         "forms": {f: {"value": P * args.steps / (r["total_ms"] / 1e3), "ms_per_step": r["total_ms"] / args.steps,
                       "blend_ms": r["blend_ms"], "kernel": r["kernel"]} for f, r in results.items()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "kernel": "blend",
+                     "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "blend",
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": alg},
         "clocks": clk,
     }
