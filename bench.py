@@ -157,7 +157,8 @@ def make_inputs(spec, seed, nbuf):
 
 
 def time_form(spec, steps, warmup, seed):
-    """Graph-replayed steps with events around the blend kernel; returns timings."""
+    """Graph-replayed steps. The timed replays carry no per-kernel events; a second set of
+    replays with events around each kernel gives the per-kernel breakdown."""
     import torch
     import paper_2103_05875_gb300 as pv
     fs, bufs = make_inputs(spec, seed, NBUF)
@@ -172,35 +173,38 @@ def time_form(spec, steps, warmup, seed):
         ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
         use_graphs = False
 
-    def step(s, e):
+    def step(s, e=None):
         rad, dist, dirs = bufs[s % NBUF]
-        e[0].record()
+        if e is not None:
+            e[0].record()
         pv.probe_update_weights(vol.handle, dirs)
-        e[1].record()
+        if e is not None:
+            e[1].record()
         pv.probe_update_blend(vol.handle, rad, dist)
-        e[2].record()
+        if e is not None:
+            e[2].record()
         vol.select_and_pack()
-        e[3].record()
+        if e is not None:
+            e[3].record()
 
-    n = warmup + steps
-    events = [[ev() for _ in range(4)] for _ in range(n)]
     with torch.cuda.stream(stream):
-        step(0, [torch.cuda.Event(enable_timing=True) for _ in range(4)])   # eager first frame
+        step(0)                                          # eager first frame
     torch.cuda.synchronize()
+    # timed: one graph per input frame, no events inside
     graphs = []
     if use_graphs:
-        for s in range(n):
+        for s in range(NBUF):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
-                step(s + 1, events[s])
+                step(s)
             graphs.append(g)
     torch.cuda.synchronize()
 
     def run(s):
         if use_graphs:
-            graphs[s].replay()
+            graphs[s % NBUF].replay()
         else:
-            step(s + 1, events[s])
+            step(s)
 
     with torch.cuda.stream(stream):
         for s in range(warmup):
@@ -209,18 +213,35 @@ def time_form(spec, steps, warmup, seed):
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         t0.record()
-        for s in range(warmup, n):
+        for s in range(warmup, warmup + steps):
             run(s)
         t1.record()
     torch.cuda.synchronize()
     total_ms = t0.elapsed_time(t1)
-    blend = [events[s][1].elapsed_time(events[s][2]) for s in range(warmup, n)]
-    weights = [events[s][0].elapsed_time(events[s][1]) for s in range(warmup, n)]
-    pack = [events[s][2].elapsed_time(events[s][3]) for s in range(warmup, n)]
-    fr = vol.select_and_pack(want_host_counts=True)   # extra call: counts of an empty frame
+    # breakdown: replays with events around each kernel
+    nb = min(steps, 16)
+    events = [[ev() for _ in range(4)] for _ in range(nb)]
+    bgraphs = []
+    for s in range(nb):
+        if use_graphs:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                step(s, events[s])
+            bgraphs.append(g)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(nb):
+            if use_graphs:
+                bgraphs[s].replay()
+            else:
+                step(s, events[s])
+    torch.cuda.synchronize()
+    blend = [events[s][1].elapsed_time(events[s][2]) for s in range(nb)]
+    weights = [events[s][0].elapsed_time(events[s][1]) for s in range(nb)]
+    pack = [events[s][2].elapsed_time(events[s][3]) for s in range(nb)]
     res = dict(total_ms=total_ms, blend_ms=statistics.mean(blend), weights_ms=statistics.mean(weights),
                select_pack_ms=statistics.mean(pack), kernel=vol.kernel, graphs=use_graphs,
-               launches_per_step=1 + 1 + 1 + 2)
+               launches_per_step=3)
     vol.close()
     del bufs
     torch.cuda.empty_cache()

@@ -28,88 +28,105 @@
 
 namespace {
 
+// 256 threads and 8 probes per block keep a 16^3 volume's 512 blocks resident
+// in one wave (several blocks per SM)
 constexpr int SP_THREADS = 256;
 constexpr int SP_WARPS = SP_THREADS / 32;
-constexpr int SP_MAX_RANGE = 512;        // probes per block
-constexpr int SP_MAX_TEX = 3 * PV_MAX_INTERIOR * PV_MAX_INTERIOR;
+constexpr int SP_RANGE = 8;              // probes per block: their codes are staged in shared memory
+constexpr int SP_MAX_T = PV_MAX_INTERIOR * PV_MAX_INTERIOR;
 
-struct SpTables {
-  uint32_t col[SP_MAX_TEX];   // colour (c, t): c << 24 | tile_pos << 12 | i << 6 | j
-  uint32_t vis[PV_MAX_INTERIOR * PV_MAX_INTERIOR];   // visibility t: tile_pos << 12 | i << 6 | j
+struct SpShared {
+  uint16_t cc[SP_RANGE][3 * SP_MAX_T];   // colour codes of the block's selected probes, slot order
+  uint16_t cv[SP_RANGE][2 * SP_MAX_T];   // visibility codes, slot order
+  int slot_c[SP_RANGE], slot_v[SP_RANGE];
+  uint16_t prev_c[SP_RANGE], prev_v[SP_RANGE];
+  int list_c[SP_RANGE], list_v[SP_RANGE];  // the block's selected probes (local index), slot order
+  int n_c, n_v, first_c, first_v;          // how many, and the slot of the first
+  int red[3 * SP_WARPS];
 };
 
-// Colour block of slot `slot` from probe p (p < 0: clear the block). Loads of
-// four codes per lane are issued before any of them is used.
-__device__ __forceinline__ void pack_color_probe(const pv_dev& k, const SpTables& tb, int p, int slot, int lane) {
-  const int by = slot / k.bw, bx = slot % k.bw;
-  const int per = 3 * k.Tc;
-  uint8_t* plane0 = reinterpret_cast<uint8_t*>(k.planes_c) + (size_t)by * k.nc * k.cpitch + (size_t)bx * k.nc * 2;
-  for (int q0 = 0; q0 < per; q0 += 128) {
-    uint32_t bits[4], ent[4];
+// Colour samples of slots [a, b) (all in one block row) from staged codes
+// cc[q0 + slot - a] (zero when `clear`). A thread owns one column of the run
+// (one division) and writes it down all 3 * n_c rows; consecutive threads
+// write consecutive 16-bit samples.
+__device__ __forceinline__ void write_color_run(const pv_dev& k, const SpShared& sh, int a, int b, int q0, bool clear) {
+  const int n = k.nc, by = a / k.bw, bx0 = a % k.bw;
+  const int cols = (b - a) * n;
+  const int groups = SP_THREADS / cols > 0 ? SP_THREADS / cols : 1;   // threads per column
+  const int x = threadIdx.x % cols, g = threadIdx.x / cols;
+  if (g >= groups) return;
+  const int so = x / n, j = x - so * n;
+  const uint16_t* src = sh.cc[q0 + so] + j;
+  uint8_t* base = reinterpret_cast<uint8_t*>(k.planes_c) + ((size_t)by * n) * k.cpitch + ((size_t)bx0 * n + x) * 2;
+  for (int row = g; row < 3 * n; row += groups) {      // row = c * n + i
+    const int c = row >= 2 * n ? 2 : (row >= n ? 1 : 0), i = row - c * n;
+    const uint32_t code = clear ? 0u : src[c * k.Tc + i * n];
+    *reinterpret_cast<uint16_t*>(base + ((size_t)c * k.ch + i) * k.cpitch) = (uint16_t)(code << k.color_shift);
+  }
+}
+
+// Visibility bytes of slots [a, b) (one block row) from staged codes. Atlas
+// row byte s (texel s / 4, byte s % 4 of (R.lo, R.hi, G.lo, G.hi)) goes to
+// plane s % 3, column s / 3. A thread owns one 32-bit word of one plane (the
+// same word in every atlas row of the run): it works out once which texel
+// byte each of the word's four bytes is, then walks the n_v rows, storing the
+// word whole when all four bytes belong to these slots and byte by byte
+// otherwise (the run's first and last words share bytes with the neighbouring
+// slots, which other blocks write).
+__device__ __forceinline__ void write_vis_run(const pv_dev& k, const SpShared& sh, int a, int b, int q0, bool clear) {
+  const int n = k.nv, by = a / k.bw, bx0 = a % k.bw;
+  const int s_lo = 4 * n * bx0, s_hi = 4 * n * (bx0 + (b - a));   // stream bytes [s_lo, s_hi)
+  const int w_lo = s_lo / 12, w_hi = (s_hi - 1) / 12;             // plane words touched (4 columns = 12 bytes)
+  const int nw = w_hi - w_lo + 1;
+  for (int q = threadIdx.x; q < 3 * nw; q += SP_THREADS) {
+    const int pl = q / nw, w = w_lo + (q - pl * nw);
+    int off[4];                                                   // staged code of each byte (-1: not ours)
+    uint32_t mask = 0, hi = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int q = q0 + lane + 32 * u;
-      ent[u] = q < per ? tb.col[q] : 0xFFFFFFFFu;
-      bits[u] = 0;
-      if (q < per && p >= 0) {
-        const uint32_t c = ent[u] >> 24, pos = (ent[u] >> 12) & 0xFFFu;
-        bits[u] = pv::load_state_bits(k.state_c, ((size_t)c * k.P + p) * k.sc_stride + pos, k.state_fmt);
-      }
+    for (int e = 0; e < 4; ++e) {
+      const int s = 3 * (4 * w + e) + pl;                         // stream byte of column 4w+e
+      off[e] = -1;
+      if (s < s_lo || s >= s_hi) continue;
+      mask |= 1u << e;
+      const int X = (s >> 2) - n * bx0;                           // texel column within the run
+      const int so = X / n, j = X - so * n;
+      off[e] = (q0 + so) * (2 * SP_MAX_T) + ((s >> 1) & 1) * k.Tv + j;
+      hi |= (uint32_t)(s & 1) << e;
     }
+    if (!mask) continue;
+    uint8_t* row = k.planes_v + ((size_t)pl * k.vh + (size_t)by * n) * k.vpitch + 4 * (size_t)w;
+    const uint16_t* cv = &sh.cv[0][0];
+    for (int i = 0; i < n; ++i) {
+      uint32_t word = 0;
+      if (!clear) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (ent[u] == 0xFFFFFFFFu) continue;
-      const uint32_t c = ent[u] >> 24, i = (ent[u] >> 6) & 63u, j = ent[u] & 63u;
-      uint16_t* dst = reinterpret_cast<uint16_t*>(plane0 + ((size_t)c * k.ch + i) * k.cpitch) + j;
-      if (p >= 0) {
-        const uint32_t code = pv::color_code_of_bits(bits[u], k.state_fmt, k.color_code);
-        *dst = (uint16_t)(code << k.color_shift);
-        k.last_c[((size_t)c * k.P + p) * k.lc_stride + i * k.nc + j] = (uint16_t)code;
+        for (int e = 0; e < 4; ++e) {
+          if (off[e] < 0) continue;
+          const uint32_t code = cv[off[e] + i * n];
+          word |= (((hi >> e) & 1u) ? (code >> 8) : (code & 0xFFu)) << (8 * e);
+        }
+      }
+      uint8_t* dst = row + (size_t)i * k.vpitch;
+      if (mask == 0xFu) {
+        *reinterpret_cast<uint32_t*>(dst) = word;
       } else {
-        *dst = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if ((mask >> e) & 1u) dst[e] = (uint8_t)(word >> (8 * e));
       }
     }
   }
 }
 
-// Visibility block of slot `slot` from probe p (p < 0: clear the block).
-__device__ __forceinline__ void pack_vis_probe(const pv_dev& k, const SpTables& tb, int p, int slot, int lane) {
-  const int by = slot / k.bw, bx = slot % k.bw;
-  const int n = k.nv;
-  for (int q0 = 0; q0 < k.Tv; q0 += 128) {
-    uint32_t b0[4], b1[4], ent[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int q = q0 + lane + 32 * u;
-      ent[u] = q < k.Tv ? tb.vis[q] : 0xFFFFFFFFu;
-      b0[u] = b1[u] = 0;
-      if (q < k.Tv && p >= 0) {
-        const uint32_t pos = ent[u] >> 12;
-        b0[u] = pv::load_state_bits(k.state_v, (size_t)p * k.sv_stride + pos, k.state_fmt);
-        b1[u] = pv::load_state_bits(k.state_v, ((size_t)k.P + p) * k.sv_stride + pos, k.state_fmt);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (ent[u] == 0xFFFFFFFFu) continue;
-      const int i = (int)((ent[u] >> 6) & 63u), j = (int)(ent[u] & 63u);
-      uint32_t c0 = 0, c1 = 0;
-      if (p >= 0) {
-        c0 = pv::vis_code_of_bits(b0[u], k.state_fmt);
-        c1 = pv::vis_code_of_bits(b1[u], k.state_fmt);
-        k.last_v[(size_t)p * k.lv_stride + i * n + j] = (uint16_t)c0;
-        k.last_v[((size_t)k.P + p) * k.lv_stride + i * n + j] = (uint16_t)c1;
-      }
-      const uint32_t bytes[4] = {c0 & 0xFFu, c0 >> 8, c1 & 0xFFu, c1 >> 8};
-      const size_t y = (size_t)by * n + i;
-      const int s0 = 4 * (bx * n + j);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int sb = s0 + b;
-        const int pl = sb % 3;
-        k.planes_v[((size_t)pl * k.vh + y) * k.vpitch + (size_t)(sb / 3)] = (uint8_t)bytes[b];
-      }
-    }
+// Slots [s0, s1) split into runs within one block row; each run written by
+// `fn` with staged codes from index q0 (+ its offset in [s0, s1)).
+template <typename F>
+__device__ __forceinline__ void for_runs(const pv_dev& k, int s0, int s1, F fn) {
+  for (int a = s0; a < s1;) {
+    const int row_end = (a / k.bw + 1) * k.bw;
+    const int b = s1 < row_end ? s1 : row_end;
+    fn(a, b, a - s0);
+    a = b;
   }
 }
 
@@ -129,29 +146,18 @@ __device__ __forceinline__ void block_reduce3(int& a, int& b, int& c, int* sh) {
   __syncthreads();
 }
 
-// Block `bid` of the `nblocks` blocks that select and pack volume k, each
-// block owning `range` consecutive probes.
-__device__ __forceinline__ void select_pack_block(const pv_dev& k, int range, int bid, int nblocks) {
-  __shared__ SpTables tb;
-  __shared__ int red[3 * SP_WARPS];
-  __shared__ int slot_c[SP_MAX_RANGE], slot_v[SP_MAX_RANGE];
-  __shared__ uint16_t prev_c[SP_MAX_RANGE], prev_v[SP_MAX_RANGE];
+// Block `bid` of the `nblocks` blocks that select and pack volume k; block
+// bid owns probes [bid * SP_RANGE, (bid + 1) * SP_RANGE).
+__device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int nblocks) {
+  __shared__ SpShared sh;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const bool fresh = *k.frame != *k.sel_frame;
   const uint32_t seq = k.sel[0];
   const uint32_t par = seq & 1u;
   const int prev_cnt_c = (int)k.sel[2 + 2 * (par ^ 1u)], prev_cnt_v = (int)k.sel[3 + 2 * (par ^ 1u)];
-  const int pb = bid * range, pe = min(k.P, pb + range);
+  const int pb = bid * SP_RANGE, pe = min(k.P, pb + SP_RANGE);
   const int W = k.chg_words, wb = pb >> 5;
 
-  for (int q = tid; q < 3 * k.Tc; q += SP_THREADS) {
-    const int c = q / k.Tc, t = q % k.Tc, i = t / k.nc, j = t % k.nc;
-    tb.col[q] = ((uint32_t)c << 24) | ((uint32_t)((i + 1) * k.tc + j + 1) << 12) | ((uint32_t)i << 6) | (uint32_t)j;
-  }
-  for (int t = tid; t < k.Tv; t += SP_THREADS) {
-    const int i = t / k.nv, j = t % k.nv;
-    tb.vis[t] = ((uint32_t)((i + 1) * k.tv + j + 1) << 12) | ((uint32_t)i << 6) | (uint32_t)j;
-  }
 
   // 1. totals, selected probes before this block's first word, last of them
   int tot_c = 0, tot_v = 0, dummy = -1;
@@ -169,58 +175,121 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int range, in
       }
     }
   }
-  block_reduce3(tot_c, tot_v, dummy, red);
+  block_reduce3(tot_c, tot_v, dummy, sh.red);
   int zero_c = 0;
-  block_reduce3(bef_c, zero_c, last_c, red);
+  block_reduce3(bef_c, zero_c, last_c, sh.red);
   int zero_v = 0;
-  block_reduce3(bef_v, zero_v, last_v, red);
+  block_reduce3(bef_v, zero_v, last_v, sh.red);
 
-  // 2. slots of this block's probes: walk its words in order (thread 0; at
-  //    most a few words per block)
-  if (tid == 0) {
-    int rc = bef_c, rv = bef_v, lc = last_c, lv = last_v;
-    for (int w = wb; w <= ((pe - 1) >> 5) && pb < pe; ++w) {
-      const uint32_t mc = fresh ? k.chg[w] : 0u, mv = fresh ? k.chg[W + w] : 0u;
-      for (int bit = 0; bit < 32; ++bit) {
-        const int p = 32 * w + bit;
-        if (p >= pe) break;
-        if (p < pb) {                                  // selected probes of this word before the range
-          if ((mc >> bit) & 1u) { ++rc; lc = p; }
-          if ((mv >> bit) & 1u) { ++rv; lv = p; }
-          continue;
-        }
-        const bool sc = (mc >> bit) & 1u, sv = (mv >> bit) & 1u;
-        if (p >= pb) {
-          slot_c[p - pb] = sc ? rc : -1;
-          slot_v[p - pb] = sv ? rv : -1;
-          prev_c[p - pb] = (uint16_t)(lc < 0 ? 0 : lc);
-          prev_v[p - pb] = (uint16_t)(lv < 0 ? 0 : lv);
-        }
-        if (sc) { ++rc; lc = p; }
-        if (sv) { ++rv; lv = p; }
-      }
+  // 2. slots of this block's probes: lane = bit of the block's word; the
+  //    selected probes before a lane come from a prefix count of the word
+  if (wid == 0) {
+    const uint32_t mc = (fresh && pb < pe) ? k.chg[wb] : 0u, mv = (fresh && pb < pe) ? k.chg[W + wb] : 0u;
+    const uint32_t below = (1u << lane) - 1u;
+    const int p = 32 * wb + lane;
+    const bool in = p >= pb && p < pe;
+    const bool selc = in && ((mc >> lane) & 1u), selv = in && ((mv >> lane) & 1u);
+    const uint32_t bal_c = __ballot_sync(0xffffffffu, selc), bal_v = __ballot_sync(0xffffffffu, selv);
+    const int rank_c = __popc(bal_c & below), rank_v = __popc(bal_v & below);
+    if (selc) sh.list_c[rank_c] = p - pb;
+    if (selv) sh.list_v[rank_v] = p - pb;
+    if (selc && rank_c == 0) sh.first_c = bef_c + __popc(mc & below);
+    if (selv && rank_v == 0) sh.first_v = bef_v + __popc(mv & below);
+    if (lane == 0) {
+      sh.n_c = __popc(bal_c);
+      sh.n_v = __popc(bal_v);
+    }
+    if (in) {
+      const uint32_t bc = mc & below, bv = mv & below;
+      sh.slot_c[p - pb] = ((mc >> lane) & 1u) ? bef_c + __popc(bc) : -1;
+      sh.slot_v[p - pb] = ((mv >> lane) & 1u) ? bef_v + __popc(bv) : -1;
+      const int lc = bc ? 32 * wb + 31 - __clz(bc) : last_c;
+      const int lv = bv ? 32 * wb + 31 - __clz(bv) : last_v;
+      sh.prev_c[p - pb] = (uint16_t)(lc < 0 ? 0 : lc);
+      sh.prev_v[p - pb] = (uint16_t)(lv < 0 ? 0 : lv);
     }
   }
   __syncthreads();
 
-  // 3. pack this block's selected probes, one warp per probe
-  for (int p = pb + wid; p < pe; p += SP_WARPS) {
-    const int sc = slot_c[p - pb], sv = slot_v[p - pb];
-    if (sc >= 0) {
-      pack_color_probe(k, tb, p, sc, lane);
-      if (lane == 0) { k.idx_c[sc] = (uint16_t)p; k.delta_c[sc] = (uint16_t)(p - prev_c[p - pb]); }
-    }
-    if (sv >= 0) {
-      pack_vis_probe(k, tb, p, sv, lane);
-      if (lane == 0) { k.idx_v[sv] = (uint16_t)p; k.delta_v[sv] = (uint16_t)(p - prev_v[p - pb]); }
+  // 3. codes of the selected probes into shared memory (slot order) and the
+  //    last-transmitted textures. A thread owns one code of the tile (channel,
+  //    texel) and walks the block's selected probes, all of its loads issued
+  //    before any is used.
+  const int n_c = sh.n_c, n_v = sh.n_v, first_c = sh.first_c, first_v = sh.first_v;
+  const int* list_c = sh.list_c;
+  const int* list_v = sh.list_v;
+  {
+    // colour: code q = c * Tc + t; the block's threads form groups of 128,
+    // group g taking probes g, g + groups, ...
+    const int M = 3 * k.Tc;
+    constexpr int groups = SP_THREADS / 128;
+    const int g = tid >> 7;
+    for (int q = tid & 127; q < M; q += 128) {
+      const int c = q >= 2 * k.Tc ? 2 : (q >= k.Tc ? 1 : 0), t = q - c * k.Tc;
+      const int i = t / k.nc, j = t - i * k.nc;
+      const size_t pos = (size_t)(i + 1) * k.tc + j + 1;
+      uint32_t bits[SP_RANGE / groups];
+#pragma unroll
+      for (int u = 0; u < SP_RANGE / groups; ++u) {
+        const int r = g + groups * u;
+        bits[u] = r < n_c ? pv::load_state_bits(k.state_c, ((size_t)c * k.P + pb + list_c[r]) * k.sc_stride + pos,
+                                                 k.state_fmt)
+                          : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < SP_RANGE / groups; ++u) {
+        const int r = g + groups * u;
+        if (r >= n_c) continue;
+        const uint32_t code = pv::color_code_of_bits(bits[u], k.state_fmt, k.color_code);
+        sh.cc[r][q] = (uint16_t)code;
+        k.last_c[((size_t)c * k.P + pb + list_c[r]) * k.lc_stride + t] = (uint16_t)code;
+      }
     }
   }
-  // 4. clear slots used by the previous frame and empty now
-  for (int s = tot_c + bid * SP_WARPS + wid; s < prev_cnt_c; s += nblocks * SP_WARPS)
-    pack_color_probe(k, tb, -1, s, lane);
-  for (int s = tot_v + bid * SP_WARPS + wid; s < prev_cnt_v; s += nblocks * SP_WARPS)
-    pack_vis_probe(k, tb, -1, s, lane);
-  // 5. counts, and the select sequence once every block is done
+  {
+    // visibility: code q = c * Tv + t, each thread taking every SP_THREADS-th
+    for (int q = tid; q < 2 * k.Tv; q += SP_THREADS) {
+      const int c = q >= k.Tv ? 1 : 0, t = q - c * k.Tv;
+      const int i = t / k.nv, j = t - i * k.nv;
+      const size_t pos = (size_t)(i + 1) * k.tv + j + 1;
+      uint32_t bits[SP_RANGE];
+#pragma unroll
+      for (int r = 0; r < SP_RANGE; ++r)
+        bits[r] = r < n_v ? pv::load_state_bits(k.state_v, ((size_t)c * k.P + pb + list_v[r]) * k.sv_stride + pos,
+                                                 k.state_fmt)
+                          : 0u;
+#pragma unroll
+      for (int r = 0; r < SP_RANGE; ++r) {
+        if (r >= n_v) continue;
+        const uint32_t code = pv::vis_code_of_bits(bits[r], k.state_fmt);
+        sh.cv[r][q] = (uint16_t)code;
+        k.last_v[((size_t)c * k.P + pb + list_v[r]) * k.lv_stride + t] = (uint16_t)code;
+      }
+    }
+  }
+  if (tid < n_c) {
+    const int lp = list_c[tid], sc = sh.slot_c[lp];
+    k.idx_c[sc] = (uint16_t)(pb + lp);
+    k.delta_c[sc] = (uint16_t)(pb + lp - sh.prev_c[lp]);
+  }
+  if (tid >= 32 && tid - 32 < n_v) {
+    const int lp = list_v[tid - 32], sv = sh.slot_v[lp];
+    k.idx_v[sv] = (uint16_t)(pb + lp);
+    k.delta_v[sv] = (uint16_t)(pb + lp - sh.prev_v[lp]);
+  }
+  __syncthreads();
+
+  // 4. the block's slots into the planes, one block row at a time
+  if (n_c > 0)
+    for_runs(k, first_c, first_c + n_c, [&](int a, int b, int q0) { write_color_run(k, sh, a, b, q0, false); });
+  if (n_v > 0)
+    for_runs(k, first_v, first_v + n_v, [&](int a, int b, int q0) { write_vis_run(k, sh, a, b, q0, false); });
+  // 5. clear slots used by the previous frame and empty now, SP_RANGE at a time
+  for (int a = tot_c + bid * SP_RANGE; a < prev_cnt_c; a += nblocks * SP_RANGE)
+    for_runs(k, a, min(prev_cnt_c, a + SP_RANGE), [&](int x, int y, int q0) { write_color_run(k, sh, x, y, q0, true); });
+  for (int a = tot_v + bid * SP_RANGE; a < prev_cnt_v; a += nblocks * SP_RANGE)
+    for_runs(k, a, min(prev_cnt_v, a + SP_RANGE), [&](int x, int y, int q0) { write_vis_run(k, sh, x, y, q0, true); });
+  // 6. counts, and the select sequence once every block is done
   if (bid == 0 && tid == 0) {
     k.counts[0] = (uint32_t)tot_c;
     k.counts[1] = (uint32_t)tot_v;
@@ -240,56 +309,38 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int range, in
   }
 }
 
-__global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k, int range) {
-  select_pack_block(k, range, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k) {
+  select_pack_block(k, blockIdx.x, gridDim.x);
 }
 
 // Several volumes in one launch: blockIdx.y is the volume.
 struct SpBatch {
   pv_dev k[PV_MAX_BATCH];
-  int range[PV_MAX_BATCH];
   int nblocks[PV_MAX_BATCH];
 };
 
 __global__ void __launch_bounds__(SP_THREADS) k_select_pack_batch(const __grid_constant__ SpBatch b) {
   const int v = blockIdx.y;
   if ((int)blockIdx.x >= b.nblocks[v]) return;
-  select_pack_block(b.k[v], b.range[v], blockIdx.x, b.nblocks[v]);
+  select_pack_block(b.k[v], blockIdx.x, b.nblocks[v]);
 }
 
-// One probe per warp keeps every probe's loads in flight at once (a warp
-// waits one memory round trip per probe); larger volumes take several.
-int sp_range(const pv_dev& k, int sms) {
-  int range = SP_WARPS;
-  while ((k.P + range - 1) / range > 16 * sms && range < SP_MAX_RANGE) range *= 2;
-  return range;
-}
-
-int device_sms() {
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms;
-}
 
 }  // namespace
 
 cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t st) {
-  const int range = sp_range(k, device_sms());
-  const int blocks = (k.P + range - 1) / range;
-  k_select_pack<<<blocks, SP_THREADS, 0, st>>>(k, range);
+  const int blocks = (k.P + SP_RANGE - 1) / SP_RANGE;
+  k_select_pack<<<blocks, SP_THREADS, 0, st>>>(k);
   return cudaGetLastError();
 }
 
 cudaError_t pv_launch_select_pack_batch(const pv_dev* ks, int n, cudaStream_t st) {
   if (n < 1 || n > PV_MAX_BATCH) return cudaErrorInvalidValue;
   SpBatch* b = new SpBatch();
-  const int sms = device_sms();
   int most = 0;
   for (int i = 0; i < n; ++i) {
     b->k[i] = ks[i];
-    b->range[i] = sp_range(ks[i], sms);
-    b->nblocks[i] = (ks[i].P + b->range[i] - 1) / b->range[i];
+    b->nblocks[i] = (ks[i].P + SP_RANGE - 1) / SP_RANGE;
     most = b->nblocks[i] > most ? b->nblocks[i] : most;
   }
   k_select_pack_batch<<<dim3(most, n), SP_THREADS, 0, st>>>(*b);
