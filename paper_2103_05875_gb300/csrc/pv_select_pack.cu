@@ -37,7 +37,7 @@ constexpr int SP_MAX_T = PV_MAX_INTERIOR * PV_MAX_INTERIOR;
 
 struct SpShared {
   uint16_t cc[SP_RANGE][3 * SP_MAX_T];   // colour codes of the block's selected probes, slot order
-  uint16_t cv[SP_RANGE][2 * SP_MAX_T];   // visibility codes, slot order
+  uint32_t cv[SP_RANGE][SP_MAX_T];       // visibility codes, slot order: R | G << 16 per texel
   int slot_c[SP_RANGE], slot_v[SP_RANGE];
   uint16_t prev_c[SP_RANGE], prev_v[SP_RANGE];
   int list_c[SP_RANGE], list_v[SP_RANGE];  // the block's selected probes (local index), slot order
@@ -65,55 +65,50 @@ __device__ __forceinline__ void write_color_run(const pv_dev& k, const SpShared&
   }
 }
 
-// Visibility bytes of slots [a, b) (one block row) from staged codes. Atlas
-// row byte s (texel s / 4, byte s % 4 of (R.lo, R.hi, G.lo, G.hi)) goes to
-// plane s % 3, column s / 3. A thread owns one 32-bit word of one plane (the
-// same word in every atlas row of the run): it works out once which texel
-// byte each of the word's four bytes is, then walks the n_v rows, storing the
-// word whole when all four bytes belong to these slots and byte by byte
-// otherwise (the run's first and last words share bytes with the neighbouring
-// slots, which other blocks write).
+// Visibility bytes of slots [a, b) (one block row) from staged codes. An
+// atlas row is the byte stream of its RG16F texels, texel X at stream bytes
+// 4X..4X+3 = (R.lo, R.hi, G.lo, G.hi), i.e. the little-endian bytes of
+// R | G << 16; stream byte s goes to plane s % 3, column s / 3. Twelve stream
+// bytes (three texels) are therefore exactly one 32-bit word of each plane, so
+// a thread owns one such chunk of one atlas row and writes three aligned words,
+// byte-permuted from the three texels; the run's first and last chunks share
+// bytes with neighbouring slots (written by other blocks) and are written byte
+// by byte, only where they belong to these slots.
 __device__ __forceinline__ void write_vis_run(const pv_dev& k, const SpShared& sh, int a, int b, int q0, bool clear) {
   const int n = k.nv, by = a / k.bw, bx0 = a % k.bw;
   const int s_lo = 4 * n * bx0, s_hi = 4 * n * (bx0 + (b - a));   // stream bytes [s_lo, s_hi)
-  const int w_lo = s_lo / 12, w_hi = (s_hi - 1) / 12;             // plane words touched (4 columns = 12 bytes)
+  const int w_lo = s_lo / 12, w_hi = (s_hi - 1) / 12;             // chunks touched
   const int nw = w_hi - w_lo + 1;
-  for (int q = threadIdx.x; q < 3 * nw; q += SP_THREADS) {
-    const int pl = q / nw, w = w_lo + (q - pl * nw);
-    int off[4];                                                   // staged code of each byte (-1: not ours)
-    uint32_t mask = 0, hi = 0;
+  const size_t plane = (size_t)k.vh * k.vpitch;
+  for (int q = threadIdx.x; q < n * nw; q += SP_THREADS) {
+    const int i = q / nw, w = w_lo + (q - i * nw);
+    uint32_t t3[3];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int s = 3 * (4 * w + e) + pl;                         // stream byte of column 4w+e
-      off[e] = -1;
-      if (s < s_lo || s >= s_hi) continue;
-      mask |= 1u << e;
-      const int X = (s >> 2) - n * bx0;                           // texel column within the run
-      const int so = X / n, j = X - so * n;
-      off[e] = (q0 + so) * (2 * SP_MAX_T) + ((s >> 1) & 1) * k.Tv + j;
-      hi |= (uint32_t)(s & 1) << e;
+    for (int e = 0; e < 3; ++e) {                                 // texels 3w, 3w+1, 3w+2 of the atlas row
+      const int X = 3 * w + e - n * bx0;                          // texel column within the run
+      t3[e] = 0u;
+      if (!clear && X >= 0 && X < n * (b - a)) {
+        const int so = X / n, j = X - so * n;
+        t3[e] = sh.cv[q0 + so][i * n + j];
+      }
     }
-    if (!mask) continue;
-    uint8_t* row = k.planes_v + ((size_t)pl * k.vh + (size_t)by * n) * k.vpitch + 4 * (size_t)w;
-    const uint16_t* cv = &sh.cv[0][0];
-    for (int i = 0; i < n; ++i) {
-      uint32_t word = 0;
-      if (!clear) {
+    const uint32_t w0 = __byte_perm(__byte_perm(t3[0], t3[1], 0x0630), t3[2], 0x5210);
+    const uint32_t w1 = __byte_perm(__byte_perm(t3[0], t3[1], 0x0741), t3[2], 0x6210);
+    const uint32_t w2 = __byte_perm(__byte_perm(t3[0], t3[1], 0x0052), t3[2], 0x7410);
+    uint8_t* dst = k.planes_v + ((size_t)by * n + i) * k.vpitch + 4 * (size_t)w;
+    if (12 * w >= s_lo && 12 * w + 12 <= s_hi) {
+      *reinterpret_cast<uint32_t*>(dst) = w0;
+      *reinterpret_cast<uint32_t*>(dst + plane) = w1;
+      *reinterpret_cast<uint32_t*>(dst + 2 * plane) = w2;
+    } else {
+      const uint32_t ws[3] = {w0, w1, w2};
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          if (off[e] < 0) continue;
-          const uint32_t code = cv[off[e] + i * n];
-          word |= (((hi >> e) & 1u) ? (code >> 8) : (code & 0xFFu)) << (8 * e);
+          const int sb = 12 * w + 3 * e + pl;                     // stream byte of this plane byte
+          if (sb >= s_lo && sb < s_hi) dst[pl * plane + e] = (uint8_t)(ws[pl] >> (8 * e));
         }
-      }
-      uint8_t* dst = row + (size_t)i * k.vpitch;
-      if (mask == 0xFu) {
-        *reinterpret_cast<uint32_t*>(dst) = word;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if ((mask >> e) & 1u) dst[e] = (uint8_t)(word >> (8 * e));
-      }
     }
   }
 }
@@ -262,7 +257,7 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
       for (int r = 0; r < SP_RANGE; ++r) {
         if (r >= n_v) continue;
         const uint32_t code = pv::vis_code_of_bits(bits[r], k.state_fmt);
-        sh.cv[r][q] = (uint16_t)code;
+        reinterpret_cast<uint16_t*>(&sh.cv[r][t])[c] = (uint16_t)code;
         k.last_v[((size_t)c * k.P + pb + list_v[r]) * k.lv_stride + t] = (uint16_t)code;
       }
     }
