@@ -39,7 +39,7 @@ pv_status cuda_fail(cudaError_t e, const char* what) {
 struct Layout {
   int P, R, nc, nv, tc, tv, Tc, Tv, bw, bh;
   int cwidth, cheight, cpitch, vwidth, vheight, vpitch;
-  int tc_pad, tv_pad, r_pad;
+  int w_rows, w_rb, w_kc, w_vb, w_chunks;
   int sb, ob;
   int sc_stride, sv_stride, lc_stride, lv_stride;
   size_t off_state_c, off_state_v, off_last_c, off_last_v, off_flags, off_wrt, off_sums, off_wop,
@@ -96,9 +96,17 @@ Layout layout_of(const pv_desc* d) {
   L.vwidth = (4 * W + 2) / 3;
   L.vheight = L.bh * L.nv;
   L.vpitch = (int)round_up((size_t)4 * ((W + 2) / 3), 16);
-  L.tc_pad = (int)round_up((size_t)L.Tc, 16);
-  L.tv_pad = (int)round_up((size_t)L.Tv, 16);
-  L.r_pad = (int)round_up((size_t)L.R, 64);
+  // tensor-core weight images: 32-byte rows of FP32 (8 rays per chunk) or
+  // 64-byte rows of 16-bit weights (32 rays per chunk); visibility texels in
+  // rows 0..Tv-1, colour texels from the next multiple of 8; 128-row tiles
+  {
+    const int eb = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
+    L.w_rb = eb == 4 ? 32 : 64;
+    L.w_kc = L.w_rb / eb;
+    L.w_vb = (int)round_up((size_t)L.Tv, 8);
+    L.w_rows = (int)round_up((size_t)L.w_vb + round_up((size_t)L.Tc, 8), 128);
+    L.w_chunks = (L.R + L.w_kc - 1) / L.w_kc;
+  }
   L.sb = d->state_fmt == PV_FMT_F16 ? 2 : 4;
   L.ob = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
   // per-probe strides padded to 16 bytes so each probe's tile and code row can
@@ -121,8 +129,8 @@ Layout layout_of(const pv_desc* d) {
   L.off_wrt = take((size_t)L.R * (L.Tc + L.Tv) * 4);
   L.off_sums = take((size_t)(L.Tc + L.Tv) * 4);
   // operand weights: F16 one binary16 plane, BF16 hi + lo bfloat16 planes, F32 hi + lo float planes
-  const size_t wop_elem = d->operand_fmt == PV_FMT_F32 ? 8 : (d->operand_fmt == PV_FMT_BF16 ? 4 : 2);
-  L.off_wop = take((size_t)(L.tc_pad + L.tv_pad) * L.r_pad * wop_elem);
+  const size_t w_planes = d->operand_fmt == PV_FMT_F16 ? 1 : 2;
+  L.off_wop = take(w_planes * L.w_chunks * L.w_rows * L.w_rb);
   L.off_hy = take(16);
   L.off_frame = take(16);
   L.off_idx_c = take((size_t)L.P * 2);
@@ -245,7 +253,7 @@ pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
   k.sel_frame = (unsigned long long*)(b + L.off_sel + 32);
   k.planes_c = (uint16_t*)(b + L.off_planes_c);
   k.planes_v = (uint8_t*)(b + L.off_planes_v);
-  k.tc_pad = L.tc_pad; k.tv_pad = L.tv_pad; k.r_pad = L.r_pad;
+  k.w_rows = L.w_rows; k.w_rb = L.w_rb; k.w_kc = L.w_kc; k.w_vb = L.w_vb; k.w_chunks = L.w_chunks;
   k.sc_stride = L.sc_stride; k.sv_stride = L.sv_stride;
   k.lc_stride = L.lc_stride; k.lv_stride = L.lv_stride;
   k.err = (int*)(b + L.off_err);

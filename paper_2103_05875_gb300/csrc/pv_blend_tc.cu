@@ -9,8 +9,10 @@
 //
 //   A (shared memory, K-major): the weights from the weights kernel, one
 //     combined texel list in 128-row tiles: visibility texels in rows
-//     0..Tv-1, colour texels from the next multiple of 8. Rows past the
-//     texels are never loaded; the lanes they produce are ignored.
+//     0..Tv-1, colour texels from the next multiple of 8. The weights kernel
+//     writes each K chunk as the exact (swizzled) shared-memory image of its
+//     tiles, so a chunk arrives with one bulk copy per plane; rows past the
+//     texels are zero and the lanes they produce are ignored.
 //   B (shared memory, K-major, one row per probe row, row groups of 32):
 //     [ d | d^2 (hi) | d^2 lo (16-bit forms) | R | G | B ]
 //     d and the colour planes come straight from HBM by TMA; d^2 is formed on
@@ -31,7 +33,8 @@
 //        accuracy.
 //
 // Warp roles (512 threads, one CTA per SM, persistent over work items):
-//   warp 0     TMA producer: ray tiles and weight tiles into a ring of stages;
+//   warp 0     producer: ray tiles (TMA) and weight images (bulk copies) into
+//              a ring of stages
 //   warp 1     TMEM allocation and the single MMA-issuing thread
 //   warps 2-3  converters: d^2 rows, TF32 hi/lo split
 //   warps 4-15 epilogue. A lane owns one texel (its TMEM lane) and a task is
@@ -75,6 +78,7 @@ template <int FORM>
 __host__ __device__ constexpr int row_bytes() { return FORM == 2 ? 32 : 64; }
 constexpr int GRP = 32;                  // probe rows per row group of the B tile
 constexpr int MT = 128;                  // texels per MMA tile (M)
+constexpr int kMaxStages = 8;            // deepest ring of K stages (shared memory permitting)
 enum TileKind { kTileVis = 0, kTileCol = 1, kTileBoth = 2 };
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 // binary16 operand form: d^2 enters the MMA scaled by 2^-4 (exact), which
@@ -87,7 +91,6 @@ struct TcParams {
   int cluster;                           // CTAs per cluster sharing each weight chunk
   int ntiles, bufcols, nbuf;             // 128-row texel tiles; TMEM columns a buffer uses
   int vb;                                // tile row of colour texel 0 (visibility texels: rows 0..Tv-1)
-  int vbox, cbox;                        // weight rows loaded per chunk: visibility, colour
   int nvc;                               // B rows (and TMEM columns) of the visibility block
   int crow;                              // first B row of the colour block
   int a_rows;                            // rows of the ray (B) tile
@@ -103,8 +106,8 @@ struct TcParams {
 // Every volume of a launch shares the tile shapes, state and operand formats
 // (the fields of TcParams); rays and probe counts may differ.
 struct BlendVol {
-  CUtensorMap rad, dist, wc, wv, wc_lo, wv_lo;
-  pv_dev k;
+  CUtensorMap rad, dist;
+  pv_dev k;                              // k.w_op: the weight tile images, one bulk copy per chunk and plane
   int item0;                             // first work item of the volume in the launch
   int nchunks;                           // ray chunks of kc rays
 };
@@ -182,16 +185,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// The same tile into the same offset of every CTA in `mask` (cluster ranks),
-// each CTA's barrier at `bar`'s offset receiving its bytes.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -205,6 +198,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_g2s_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                            uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
@@ -581,12 +582,6 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
       for (int v = 0; v < a.nvol; ++v) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].dist) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].rad) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].wc) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].wv) : "memory");
-        if (kSplitW) {
-          asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].wc_lo) : "memory");
-          asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].wv_lo) : "memory");
-        }
       }
       int s = 0;
       uint32_t ph = 0;
@@ -612,25 +607,17 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
             for (int c = 0; c < 3; ++c)
               tma_load_2d(st + (size_t)(tp.crow + c * GRP) * ROWB, &bv.rad, x, c * bv.k.P + p0, &full[s]);
           }
-          // weight rows: visibility texels from tile row 0, colour texels from row vb
-          uint8_t* wv = st + tp.off_w;
-          uint8_t* wc = st + tp.off_w + (size_t)tp.vb * ROWB;
-          uint8_t* wv_lo = st + tp.off_w_lo;
-          uint8_t* wc_lo = st + tp.off_w_lo + (size_t)tp.vb * ROWB;
+          // the chunk's weight tile images (hi and, split forms, lo), one bulk
+          // copy each, straight into the MMA's swizzled layout
+          const uint32_t wbytes = (uint32_t)tp.ntiles * MT * ROWB;
+          const uint8_t* wsrc = (const uint8_t*)bv.k.w_op + (size_t)kc * wbytes;
+          const size_t wplane = (size_t)bv.k.w_chunks * wbytes;
           if (tp.cluster == 1) {
-            tma_load_2d(wv, &bv.wv, x, 0, &full[s]);
-            tma_load_2d(wc, &bv.wc, x, 0, &full[s]);
-            if (kSplitW) {
-              tma_load_2d(wv_lo, &bv.wv_lo, x, 0, &full[s]);
-              tma_load_2d(wc_lo, &bv.wc_lo, x, 0, &full[s]);
-            }
+            bulk_g2s(st + tp.off_w, wsrc, wbytes, &full[s]);
+            if (kSplitW) bulk_g2s(st + tp.off_w_lo, wsrc + wplane, wbytes, &full[s]);
           } else if ((uint32_t)(kc % tp.cluster) == crank) {
-            tma_load_2d_mc(wv, &bv.wv, x, 0, &full[s], cmask);
-            tma_load_2d_mc(wc, &bv.wc, x, 0, &full[s], cmask);
-            if (kSplitW) {
-              tma_load_2d_mc(wv_lo, &bv.wv_lo, x, 0, &full[s], cmask);
-              tma_load_2d_mc(wc_lo, &bv.wc_lo, x, 0, &full[s], cmask);
-            }
+            bulk_g2s_mc(st + tp.off_w, wsrc, wbytes, &full[s], cmask);
+            if (kSplitW) bulk_g2s_mc(st + tp.off_w_lo, wsrc + wplane, wbytes, &full[s], cmask);
           }
           if (++s == tp.stages) {
             s = 0;
@@ -1031,24 +1018,21 @@ cudaError_t dev_info(DevInfo* d) {
 // Fills every field of tp except items, iters and the volume-dependent ones.
 cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int smem_max, TcParams& tp,
                         size_t* smem) {
-  const int ob = form == kF32 ? 4 : 2;
   const int sb = k.state_fmt == PV_FMT_F16 ? 2 : 4;
   const int ROWB = form == kF32 ? row_bytes<kF32>() : row_bytes<kF16>();
   tp.k = k;
   tp.cluster = cluster;
-  tp.kc = ROWB / ob;
+  tp.kc = k.w_kc;                              // = ROWB / operand bytes
   // ray (B) tile rows: d | d^2 (| d^2 lo, 16-bit forms) | R | G | B, 32 each
   tp.nvc = form != kF32 ? 3 * GRP : 2 * GRP;
   tp.crow = tp.nvc;
   tp.a_rows = tp.crow + 3 * GRP;
-  // texel (A) tiles: visibility texels in rows 0..Tv-1, colour texels from
-  // row vb (8-row aligned, so that their TMA destination stays aligned); one
-  // MMA per 128-row tile, with the B rows its texels need
-  tp.vbox = (k.Tv + 7) / 8 * 8;
-  tp.cbox = (k.Tc + 7) / 8 * 8;
-  tp.vb = tp.vbox;
-  const int rows = tp.vb + tp.cbox;
-  tp.ntiles = (rows + MT - 1) / MT;
+  // texel (A) tiles: the weight images' rows, visibility texels in rows
+  // 0..Tv-1 and colour texels from row vb; one MMA per 128-row tile, with the
+  // B rows its texels need
+  if (k.w_rb != ROWB || k.w_rows % MT != 0) return cudaErrorInvalidValue;
+  tp.vb = k.w_vb;
+  tp.ntiles = k.w_rows / MT;
   int col = 0;
   for (int j = 0; j < tp.ntiles; ++j) {
     const int r0 = j * MT, r1 = r0 + MT;
@@ -1099,10 +1083,10 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int
     if (stages >= 2) break;
   }
   if (stages < 2) return cudaErrorInvalidConfiguration;
-  if (stages > 4) stages = 4;
+  if (stages > kMaxStages) stages = kMaxStages;
   tp.np = np;
   tp.stages = stages;
-  tp.w_tx = (uint32_t)((form != kF16 ? 2 : 1) * (tp.vbox + tp.cbox) * ROWB);
+  tp.w_tx = (uint32_t)((form != kF16 ? 2 : 1) * tp.ntiles * MT * ROWB);
   tp.stage_tx = (uint32_t)(4 * np * ROWB) + tp.w_tx;
   off = (size_t)stages * tp.stage_bytes;
   tp.off_state = (int)off;
@@ -1121,28 +1105,6 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int
   off += 1024;
   *smem = off + 1024;                          // slack for aligning the dynamic base
   return cudaSuccess;
-}
-
-// The volume's weight tensor maps (fixed for the volume's life).
-cudaError_t encode_w_maps(const pv_dev& k, int form, const TcParams& tp, BlendVol& bv) {
-  const int ob = form == kF32 ? 4 : 2;
-  const size_t wplane = (size_t)(k.tc_pad + k.tv_pad) * k.r_pad;
-  const uint8_t* w = (const uint8_t*)k.w_op;
-  cudaError_t e = encode_2d(&bv.wc, k.operand_fmt, w, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.cbox);
-  if (e == cudaSuccess)
-    e = encode_2d(&bv.wv, k.operand_fmt, w + (size_t)k.tc_pad * k.r_pad * ob, k.r_pad, k.tv_pad,
-                  (uint64_t)k.r_pad * ob, tp.kc, tp.vbox);
-  if (e == cudaSuccess && form != kF16) {
-    e = encode_2d(&bv.wc_lo, k.operand_fmt, w + wplane * ob, k.r_pad, k.tc_pad, (uint64_t)k.r_pad * ob, tp.kc,
-                  tp.cbox);
-    if (e == cudaSuccess)
-      e = encode_2d(&bv.wv_lo, k.operand_fmt, w + (wplane + (size_t)k.tc_pad * k.r_pad) * ob, k.r_pad,
-                    k.tv_pad, (uint64_t)k.r_pad * ob, tp.kc, tp.vbox);
-  } else {
-    bv.wc_lo = bv.wc;
-    bv.wv_lo = bv.wv;
-  }
-  return e;
 }
 
 // Tensor maps of one frame's rays (radiance [3][P][R], dist [P][R]).
@@ -1260,8 +1222,7 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
     BlendVol& bv = pl->args.v[0];
     bv.k = k;
     bv.item0 = 0;
-    bv.nchunks = (k.R + tp.kc - 1) / tp.kc;
-    e = encode_w_maps(k, form, tp, bv);
+    bv.nchunks = k.w_chunks;
   }
   if (e != cudaSuccess) {
     delete pl;
@@ -1315,9 +1276,8 @@ cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc
       BlendVol& bv = b->args.v[i];
       bv.k = k;
       bv.item0 = items;
-      bv.nchunks = (k.R + tp.kc - 1) / tp.kc;
+      bv.nchunks = k.w_chunks;
       items += (k.P + tp.np - 1) / tp.np;
-      e = encode_w_maps(k, form, tp, bv);
       b->vols[i] = vols[i];
     }
     tp.items = items;

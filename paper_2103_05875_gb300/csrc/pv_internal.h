@@ -28,8 +28,10 @@ struct pv_dev {
   int chg_words;                        // words per texture: ceil(P / 32)
   float* w_rt;                          // [R][Tc + Tv] weights, ray-major (SIMT blend)
   float* sums;                          // [Tc + Tv] weight sums
-  void* w_op;                           // [planes][tc_pad + tv_pad][r_pad] weights, texel-major, operand
-                                        // format: F16 one plane; BF16 and F32 hi and lo planes
+  void* w_op;                           // weights in the operand format for the tensor-core blend, as
+                                        // shared-memory tile images: [planes][w_chunks][w_rows x w_rb
+                                        // bytes] (F16 one plane; BF16 and F32 hi and lo planes); see
+                                        // pv_w_image_offset
   float* hy;                            // [1] hysteresis of the frame being blended
   unsigned long long* frame;            // [1] device frame counter
   uint16_t* idx_c;                      // [P]
@@ -42,7 +44,9 @@ struct pv_dev {
   unsigned long long* sel_frame;        // [1]: frame counter value at the last select
   uint16_t* planes_c;                   // 3 planes of ch rows x cpitch bytes
   uint8_t* planes_v;                    // 3 planes of vh rows x vpitch bytes
-  int tc_pad, tv_pad, r_pad;            // padded shapes of w_op
+  int w_rows, w_rb, w_kc, w_vb, w_chunks;   // w_op images: rows (visibility texels from row 0,
+                                        // colour texels from row w_vb), bytes per row, rays per chunk,
+                                        // chunks per plane
   int sc_stride, sv_stride;             // elements per probe tile in state memory (16-byte multiple)
   int lc_stride, lv_stride;             // codes per probe in the last-transmitted arrays (multiple of 8)
   int* err;                             // [1] device error word (non-zero: a bounded wait gave up)
@@ -64,6 +68,18 @@ struct pv_volume {
   unsigned long long frame;             // host mirror of the frame counter
   void* tc_plan;                        // tensor-core kernel plan (tensor maps), or NULL
 };
+
+// Byte offset of ray r of image row `row` in one plane of w_op. Each chunk of
+// w_kc rays is a w_rows x w_rb tile with the 16-byte units of a row XORed by
+// address bits 7.. (the SWIZZLE_32B / SWIZZLE_64B shared-memory layouts the
+// tensor-core blend's MMA descriptors read), so a chunk moves into shared
+// memory with one bulk copy.
+__host__ __device__ inline size_t pv_w_image_offset(const pv_dev& k, int row, int r, int elem_bytes) {
+  const int chunk = r / k.w_kc, kk = r - chunk * k.w_kc;
+  const uint32_t o = (uint32_t)(row * k.w_rb + kk * elem_bytes);
+  const uint32_t m = (uint32_t)(k.w_rb / 16 - 1);
+  return (size_t)chunk * k.w_rows * k.w_rb + (o ^ (((o >> 7) & m) << 4));
+}
 
 // ---------------------------------------------------------------- launchers
 cudaError_t pv_launch_weights(const pv_dev& k, const float* dirs, int want_rt, int want_op,

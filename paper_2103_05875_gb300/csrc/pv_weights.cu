@@ -91,10 +91,11 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
   const float sq_lo = fmaf(-sq, sq, Q) / (2.0f * sq);   // sqrt(Q) ~= sq + sq_lo
   const float s = k.sharpness;
 
-  // Operand-format copy for the tensor-core blend: texel-major rows of r_pad
-  // rays; colour rows first (tc_pad of them), then visibility rows.
-  const size_t op_row = vis ? (size_t)(k.tc_pad + t) : (size_t)t;
-  const size_t plane = (size_t)(k.tc_pad + k.tv_pad) * k.r_pad;   // elements per operand plane
+  // Operand-format copy for the tensor-core blend: shared-memory tile images
+  // (pv_w_image_offset), visibility texels in rows 0.., colour from w_vb.
+  const int op_row = vis ? t : k.w_vb + t;
+  const int eb = k.operand_fmt == PV_FMT_F32 ? 4 : 2;
+  const size_t plane = (size_t)k.w_chunks * k.w_rows * k.w_rb;   // bytes per operand plane
 
   float part = 0.0f;
   for (int r = threadIdx.x; r < k.R; r += blockDim.x) {
@@ -121,9 +122,9 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
     const OpWeight o = split_weight(w, k.operand_fmt, vis);
     if (want_rt) k.w_rt[(size_t)r * T + tg] = o.eff;
     if (want_op) {
-      store_plane(k.w_op, op_row * k.r_pad + r, o.hi, k.operand_fmt);
-      if (k.operand_fmt != PV_FMT_F16)
-        store_plane(k.w_op, plane + op_row * k.r_pad + r, o.lo, k.operand_fmt);
+      uint8_t* img = reinterpret_cast<uint8_t*>(k.w_op) + pv_w_image_offset(k, op_row, r, eb);
+      store_plane(img, 0, o.hi, k.operand_fmt);
+      if (k.operand_fmt != PV_FMT_F16) store_plane(img + plane, 0, o.lo, k.operand_fmt);
     }
     part += o.eff;
   }
