@@ -96,12 +96,12 @@ Layout layout_of(const pv_desc* d) {
   L.vwidth = (4 * W + 2) / 3;
   L.vheight = L.bh * L.nv;
   L.vpitch = (int)round_up((size_t)4 * ((W + 2) / 3), 16);
-  // tensor-core weight images: 32-byte rows of FP32 (8 rays per chunk) or
-  // 64-byte rows of 16-bit weights (32 rays per chunk); visibility texels in
+  // tensor-core weight images: 64-byte rows (16 FP32 or 32 16-bit weights
+  // per chunk); visibility texels in
   // rows 0..Tv-1, colour texels from the next multiple of 8; 128-row tiles
   {
     const int eb = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
-    L.w_rb = eb == 4 ? 32 : 64;
+    L.w_rb = 64;
     L.w_kc = L.w_rb / eb;
     L.w_vb = (int)round_up((size_t)L.Tv, 8);
     L.w_rows = (int)round_up((size_t)L.w_vb + round_up((size_t)L.Tc, 8), 128);

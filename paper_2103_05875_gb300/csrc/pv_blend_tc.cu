@@ -71,11 +71,12 @@ enum Form { kF16 = 0, kBF16 = 1, kF32 = 2 };
 constexpr int NT = 512;
 constexpr int EPI_WARPS = 12;            // warps 4..15, three per TMEM lane quarter
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
-// bytes per K-chunk row in shared memory: 64 (SWIZZLE_64B) for the 16-bit
-// forms, 32 (SWIZZLE_32B) for TF32, which keeps the FP32 form's stages small
-// enough for a four-deep ring
+// bytes per K-chunk row in shared memory: 64 (SWIZZLE_64B) for every form,
+// i.e. 32 rays per chunk for 16-bit operands and 16 for TF32. Per-chunk
+// latency dominates the main loop, so fewer, larger chunks win over a deeper
+// ring (the FP32 form then fits two stages)
 template <int FORM>
-__host__ __device__ constexpr int row_bytes() { return FORM == 2 ? 32 : 64; }
+__host__ __device__ constexpr int row_bytes() { return 64; }
 constexpr int GRP = 32;                  // probe rows per row group of the B tile
 constexpr int MT = 128;                  // texels per MMA tile (M)
 constexpr int kMaxStages = 8;            // deepest ring of K stages (shared memory permitting)
