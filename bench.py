@@ -32,6 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 NBUF = 8
+FPG = 4          # frames per captured graph in the timed replays
 # DRAM bytes (read + write) of one k_blend_tc launch of the FP32 form from one ncu capture
 # (profiles/blend_tc_16x16x16_256rays.md), valid only for the kernel source it was taken
 # on: reported as null once the source has changed.
@@ -190,31 +191,49 @@ def time_form(spec, steps, warmup, seed):
     with torch.cuda.stream(stream):
         step(0)                                          # eager first frame
     torch.cuda.synchronize()
-    # timed: one graph per input frame, no events inside
-    graphs = []
+    # timed: graphs of FPG consecutive frames (and single-frame graphs for a
+    # remainder), no events inside; inside a graph the kernels of consecutive
+    # frames are chained by programmatic dependent launch
+    graphs, singles = [], []
     if use_graphs:
+        for gi in range(NBUF // FPG):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for f in range(FPG):
+                    step(gi * FPG + f)
+            graphs.append(g)
         for s in range(NBUF):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
                 step(s)
-            graphs.append(g)
+            singles.append(g)
     torch.cuda.synchronize()
 
-    def run(s):
-        if use_graphs:
-            graphs[s % NBUF].replay()
-        else:
-            step(s)
+    def run(first, count):
+        s = first
+        while count > 0:
+            if use_graphs and count >= FPG and s % FPG == 0:
+                graphs[(s % NBUF) // FPG].replay()
+                s += FPG
+                count -= FPG
+            elif use_graphs:
+                singles[s % NBUF].replay()
+                s += 1
+                count -= 1
+            else:
+                step(s)
+                s += 1
+                count -= 1
 
     with torch.cuda.stream(stream):
-        for s in range(warmup):
-            run(s)
+        run(0, warmup)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    first = (warmup + FPG - 1) // FPG * FPG
     with torch.cuda.stream(stream):
+        run(warmup, first - warmup)                      # untimed, aligns the timed steps to graphs
         t0.record()
-        for s in range(warmup, warmup + steps):
-            run(s)
+        run(first, steps)
         t1.record()
     torch.cuda.synchronize()
     total_ms = t0.elapsed_time(t1)
@@ -566,6 +585,7 @@ def run_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": forms[0], "mode": "noisy (fresh rays every frame)",
                    "l2": f"inputs larger than L2: {NBUF} distinct frames cycled",
+                   "graph": f"{FPG} frames per captured CUDA graph, kernels chained by programmatic dependent launch",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single volume",
                    "graphs": head["graphs"], "blend_kernel": head["kernel"]},
         "gpu_launches": head["launches_per_step"] * args.steps,

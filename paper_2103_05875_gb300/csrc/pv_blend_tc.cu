@@ -515,6 +515,7 @@ template <int FORM, int MAXV>
 __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ BlendArgs<MAXV> a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  pv_grid_launch_dependents();
   const TcParams& tp = a.tp;
   const pv_dev& k = tp.k;                          // shapes and formats shared by the volumes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -570,6 +571,9 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+  // everything above ran while the previous kernel may still be running;
+  // from here on the kernel reads what it (and the kernels before it) wrote
+  pv_grid_wait();
   int* err = k.err;
   const uint32_t crank = tp.cluster > 1 ? cluster_rank() : 0u;
   const uint16_t cmask = (uint16_t)((1u << tp.cluster) - 1u);
@@ -1120,17 +1124,18 @@ cudaError_t encode_ray_maps(const pv_dev& k, int form, const TcParams& tp, const
 template <int MAXV>
 cudaError_t launch_blend(const BlendArgs<MAXV>& a, int form, int grid, size_t smem, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = a.tp.cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1] = pv_pdl_attr();
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   cudaError_t e;
   if (form == kF16) e = cudaLaunchKernelEx(&cfg, k_blend_tc<kF16, MAXV>, a);
   else if (form == kBF16) e = cudaLaunchKernelEx(&cfg, k_blend_tc<kBF16, MAXV>, a);

@@ -81,6 +81,22 @@ __host__ __device__ inline size_t pv_w_image_offset(const pv_dev& k, int row, in
   return (size_t)chunk * k.w_rows * k.w_rb + (o ^ (((o >> 7) & m) << 4));
 }
 
+// Programmatic dependent launch: a kernel launched with
+// pv_pdl_attr may start while its predecessor in the stream is still running;
+// it lets its own successor start early (pv_grid_launch_dependents) and must
+// call pv_grid_wait before it reads anything the predecessor (or anything
+// before it) wrote. Both are no-ops for a kernel launched without the attribute.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pv_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pv_grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+inline cudaLaunchAttribute pv_pdl_attr() {
+  cudaLaunchAttribute a;
+  a.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  a.val.programmaticStreamSerializationAllowed = 1;
+  return a;
+}
+
 // ---------------------------------------------------------------- launchers
 cudaError_t pv_launch_weights(const pv_dev& k, const float* dirs, int want_rt, int want_op,
                               cudaStream_t s);

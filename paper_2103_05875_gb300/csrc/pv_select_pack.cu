@@ -305,6 +305,8 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
 }
 
 __global__ void __launch_bounds__(SP_THREADS) k_select_pack(pv_dev k) {
+  pv_grid_launch_dependents();
+  pv_grid_wait();
   select_pack_block(k, blockIdx.x, gridDim.x);
 }
 
@@ -315,6 +317,8 @@ struct SpBatch {
 };
 
 __global__ void __launch_bounds__(SP_THREADS) k_select_pack_batch(const __grid_constant__ SpBatch b) {
+  pv_grid_launch_dependents();
+  pv_grid_wait();
   const int v = blockIdx.y;
   if ((int)blockIdx.x >= b.nblocks[v]) return;
   select_pack_block(b.k[v], blockIdx.x, b.nblocks[v]);
@@ -325,8 +329,15 @@ __global__ void __launch_bounds__(SP_THREADS) k_select_pack_batch(const __grid_c
 
 cudaError_t pv_launch_select_pack(const pv_dev& k, cudaStream_t st) {
   const int blocks = (k.P + SP_RANGE - 1) / SP_RANGE;
-  k_select_pack<<<blocks, SP_THREADS, 0, st>>>(k);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1] = {pv_pdl_attr()};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(SP_THREADS);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_select_pack, k);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t pv_launch_select_pack_batch(const pv_dev* ks, int n, cudaStream_t st) {
@@ -338,9 +349,16 @@ cudaError_t pv_launch_select_pack_batch(const pv_dev* ks, int n, cudaStream_t st
     b->nblocks[i] = (ks[i].P + SP_RANGE - 1) / SP_RANGE;
     most = b->nblocks[i] > most ? b->nblocks[i] : most;
   }
-  k_select_pack_batch<<<dim3(most, n), SP_THREADS, 0, st>>>(*b);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1] = {pv_pdl_attr()};
+  cfg.gridDim = dim3(most, n);
+  cfg.blockDim = dim3(SP_THREADS);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_select_pack_batch, *b);
   delete b;
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 namespace {

@@ -150,6 +150,8 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
 
 __global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restrict__ dirs,
                                                  int want_rt, int want_op) {
+  pv_grid_launch_dependents();
+  pv_grid_wait();
   weights_block(k, dirs, want_rt, want_op, blockIdx.x, blockIdx.x == 0);
 }
 
@@ -161,6 +163,8 @@ struct WeightsBatch {
 
 __global__ void __launch_bounds__(256) k_weights_batch(const __grid_constant__ WeightsBatch b, int want_rt,
                                                        int want_op) {
+  pv_grid_launch_dependents();
+  pv_grid_wait();
   const pv_dev& k = b.k[blockIdx.y];
   if ((int)blockIdx.x >= k.Tc + k.Tv) return;
   weights_block(k, b.dirs[blockIdx.y], want_rt, want_op, blockIdx.x, blockIdx.x == 0);
@@ -178,13 +182,27 @@ cudaError_t pv_launch_weights_batch(const pv_dev* ks, const float* const* dirs, 
     b->dirs[i] = dirs[i];
     most = ks[i].Tc + ks[i].Tv > most ? ks[i].Tc + ks[i].Tv : most;
   }
-  k_weights_batch<<<dim3(most, n), 256, 0, st>>>(*b, want_rt, want_op);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1] = {pv_pdl_attr()};
+  cfg.gridDim = dim3(most, n);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_weights_batch, *b, want_rt, want_op);
   delete b;
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t pv_launch_weights(const pv_dev& k, const float* dirs, int want_rt, int want_op,
                               cudaStream_t st) {
-  k_weights<<<k.Tc + k.Tv, 256, 0, st>>>(k, dirs, want_rt, want_op);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1] = {pv_pdl_attr()};
+  cfg.gridDim = dim3(k.Tc + k.Tv);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_weights, k, dirs, want_rt, want_op);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
