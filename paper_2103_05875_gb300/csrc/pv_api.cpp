@@ -42,7 +42,7 @@ struct Layout {
   int w_rows, w_rb, w_kc, w_vb, w_chunks;
   int sb, ob;
   int sc_stride, sv_stride, lc_stride, lv_stride;
-  size_t off_state_c, off_state_v, off_last_c, off_last_v, off_flags, off_wrt, off_sums, off_wop,
+  size_t off_state_c, off_state_v, off_last_c, off_last_v, off_cur_c, off_cur_v, off_flags, off_wrt, off_sums, off_wop,
       off_hy, off_frame, off_idx_c, off_idx_v, off_delta_c, off_delta_v, off_counts, off_planes_c,
       off_planes_v, off_err, off_sel, total;
 };
@@ -125,6 +125,8 @@ Layout layout_of(const pv_desc* d) {
   L.off_state_v = take((size_t)2 * L.P * L.sv_stride * L.sb);
   L.off_last_c = take((size_t)3 * L.P * L.lc_stride * 2);
   L.off_last_v = take((size_t)2 * L.P * L.lv_stride * 2);
+  L.off_cur_c = take((size_t)3 * L.P * L.lc_stride * 2);
+  L.off_cur_v = take((size_t)2 * L.P * L.lv_stride * 2);
   L.off_flags = take((size_t)2 * ((L.P + 31) / 32) * 4);
   L.off_wrt = take((size_t)L.R * (L.Tc + L.Tv) * 4);
   L.off_sums = take((size_t)(L.Tc + L.Tv) * 4);
@@ -237,6 +239,8 @@ pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
   k.state_v = b + L.off_state_v;
   k.last_c = (uint16_t*)(b + L.off_last_c);
   k.last_v = (uint16_t*)(b + L.off_last_v);
+  k.cur_c = (uint16_t*)(b + L.off_cur_c);
+  k.cur_v = (uint16_t*)(b + L.off_cur_v);
   k.chg = (uint32_t*)(b + L.off_flags);
   k.chg_words = (L.P + 31) / 32;
   k.w_rt = (float*)(b + L.off_wrt);
@@ -262,6 +266,8 @@ pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
   e = cudaMemset(v->base, 0, L.total);
   if (e == cudaSuccess) e = cudaMemset(k.last_c, 0xFF, (size_t)3 * L.P * L.lc_stride * 2);
   if (e == cudaSuccess) e = cudaMemset(k.last_v, 0xFF, (size_t)2 * L.P * L.lv_stride * 2);
+  if (e == cudaSuccess) e = cudaMemset(k.cur_c, 0xFF, (size_t)3 * L.P * L.lc_stride * 2);
+  if (e == cudaSuccess) e = cudaMemset(k.cur_v, 0xFF, (size_t)2 * L.P * L.lv_stride * 2);
   if (e == cudaSuccess) {
     const unsigned long long never = ~0ull;           // no select yet: flags are fresh
     e = cudaMemcpy(k.sel_frame, &never, sizeof never, cudaMemcpyHostToDevice);

@@ -72,15 +72,16 @@ void fill_frame(pv_volume* v, pv_frame* out) {
 }
 
 // Device bytes a volume's blend writes besides the weights: its tiles, its
-// changed-probe bits, its frame counter and hysteresis.
+// current codes, its changed-probe bits, its frame counter and hysteresis.
 struct Saved {
-  size_t tc, tv, chg;
+  size_t tc, tv, cc, cv, chg;
 };
 
 Saved saved_sizes(const pv_volume* v) {
   const pv_dev& k = v->k;
   const size_t sb = (size_t)v->state_bytes;
   return Saved{(size_t)3 * k.P * k.sc_stride * sb, (size_t)2 * k.P * k.sv_stride * sb,
+               (size_t)3 * k.P * k.lc_stride * 2, (size_t)2 * k.P * k.lv_stride * 2,
                (size_t)2 * k.chg_words * sizeof(uint32_t)};
 }
 
@@ -162,7 +163,7 @@ pv_status probe_batch_tune(pv_batch* b, const void* const* radiance, const void*
   Saved sz[PV_MAX_BATCH];
   for (int i = 0; i < b->n; ++i) {
     sz[i] = saved_sizes(b->vols[i]);
-    total += sz[i].tc + sz[i].tv + sz[i].chg + 64;
+    total += sz[i].tc + sz[i].tv + sz[i].cc + sz[i].cv + sz[i].chg + 64;
   }
   char* save = nullptr;
   cudaError_t e = cudaMalloc(&save, total);
@@ -172,9 +173,9 @@ pv_status probe_batch_tune(pv_batch* b, const void* const* radiance, const void*
     char* p = save;
     for (int i = 0; i < b->n && r == cudaSuccess; ++i) {
       const pv_dev& k = b->vols[i]->k;
-      void* dev[4] = {k.state_c, k.state_v, k.chg, k.frame};
-      const size_t n[4] = {sz[i].tc, sz[i].tv, sz[i].chg, sizeof(unsigned long long)};
-      for (int q = 0; q < 4 && r == cudaSuccess; ++q) {
+      void* dev[6] = {k.state_c, k.state_v, k.cur_c, k.cur_v, k.chg, k.frame};
+      const size_t n[6] = {sz[i].tc, sz[i].tv, sz[i].cc, sz[i].cv, sz[i].chg, sizeof(unsigned long long)};
+      for (int q = 0; q < 6 && r == cudaSuccess; ++q) {
         r = to_save ? cudaMemcpyAsync(p, dev[q], n[q], cudaMemcpyDeviceToDevice, st)
                     : cudaMemcpyAsync(dev[q], p, n[q], cudaMemcpyDeviceToDevice, st);
         p += n[q];

@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(NT) k_blend_simt(pv_dev k, const Tin* __restri
       const uint32_t code = vis ? pv::vis_code_of_bits(nb_bits, k.state_fmt)
                                 : pv::color_code_of_bits(nb_bits, k.state_fmt, k.color_code);
       if (code != prev[g]) flag_s[((vis ? 3 : 0) + ch) * G + g] = 1;
+      if (k.cur_c) (vis ? k.cur_v : k.cur_c)[((size_t)ch * k.P + p) * lstride + t] = (uint16_t)code;
     }
   }
   __syncthreads();

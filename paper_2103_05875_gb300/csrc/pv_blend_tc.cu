@@ -376,6 +376,7 @@ __device__ __forceinline__ uint32_t epi_task(uint32_t taddr, uint32_t taddr_lo, 
       sts_if<SB>(live, tb + ro[u], nb);
       const uint32_t code = texel_code<SF, KIND, VIS>(nb);
       mg |= (live && code != last[u]) ? (1u << u) : 0u;
+      sts_if<2>(live, cb + co[u], code);             // the code tile now holds the current codes
     }
     m |= mg << g;
   }
@@ -899,6 +900,13 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         for (int c = 0; c < 2; ++c)
           bulk_s2g((uint8_t*)kv.state_v + ((size_t)c * kv.P + p0) * k.sv_stride * sb,
                    st_v + (size_t)c * np * k.sv_stride * sb, sv_b);
+        if (kv.cur_c) {                                // the item's current codes
+          const uint32_t lc_b = (uint32_t)npi * k.lc_stride * 2, lv_b = (uint32_t)npi * k.lv_stride * 2;
+          for (int c = 0; c < 3; ++c)
+            bulk_s2g(kv.cur_c + ((size_t)c * kv.P + p0) * k.lc_stride, ls_c + (size_t)c * np * k.lc_stride, lc_b);
+          for (int c = 0; c < 2; ++c)
+            bulk_s2g(kv.cur_v + ((size_t)c * kv.P + p0) * k.lv_stride, ls_v + (size_t)c * np * k.lv_stride, lv_b);
+        }
         bulk_commit();
         bulk_wait_read();                              // shared tiles may be refilled now
         const int next = item + gridDim.x;

@@ -23,6 +23,8 @@ struct pv_dev {
   void* state_v;                        // [2][P][sv_stride]
   uint16_t* last_c;                     // [3][P][lc_stride], first Tc codes used
   uint16_t* last_v;                     // [2][P][lv_stride]
+  uint16_t* cur_c;                      // [3][P][lc_stride]: transmitted codes of the current texels
+  uint16_t* cur_v;                      // [2][P][lv_stride] (written by the blend; NULL: not kept)
   uint32_t* chg;                        // [2][chg_words]: changed-probe bits, colour then
                                         // visibility, bit p%32 of word p/32
   int chg_words;                        // words per texture: ceil(P / 32)

@@ -36,7 +36,8 @@ constexpr int SP_RANGE = 8;              // probes per block: their codes are st
 constexpr int SP_MAX_T = PV_MAX_INTERIOR * PV_MAX_INTERIOR;
 
 struct SpShared {
-  uint16_t cc[SP_RANGE][3 * SP_MAX_T];   // colour codes of the block's selected probes, slot order
+  uint16_t cc[SP_RANGE][3 * SP_MAX_T];   // colour codes of the block's selected probes, slot order,
+                                         // channel rows lc_stride apart
   uint32_t cv[SP_RANGE][SP_MAX_T];       // visibility codes, slot order: R | G << 16 per texel
   int slot_c[SP_RANGE], slot_v[SP_RANGE];
   uint16_t prev_c[SP_RANGE], prev_v[SP_RANGE];
@@ -60,7 +61,7 @@ __device__ __forceinline__ void write_color_run(const pv_dev& k, const SpShared&
   uint8_t* base = reinterpret_cast<uint8_t*>(k.planes_c) + ((size_t)by * n) * k.cpitch + ((size_t)bx0 * n + x) * 2;
   for (int row = g; row < 3 * n; row += groups) {      // row = c * n + i
     const int c = row >= 2 * n ? 2 : (row >= n ? 1 : 0), i = row - c * n;
-    const uint32_t code = clear ? 0u : src[c * k.Tc + i * n];
+    const uint32_t code = clear ? 0u : src[c * k.lc_stride + i * n];
     *reinterpret_cast<uint16_t*>(base + ((size_t)c * k.ch + i) * k.cpitch) = (uint16_t)(code << k.color_shift);
   }
 }
@@ -144,7 +145,7 @@ __device__ __forceinline__ void block_reduce3(int& a, int& b, int& c, int* sh) {
 // Block `bid` of the `nblocks` blocks that select and pack volume k; block
 // bid owns probes [bid * SP_RANGE, (bid + 1) * SP_RANGE).
 __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int nblocks) {
-  __shared__ SpShared sh;
+  __shared__ __align__(16) SpShared sh;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const bool fresh = *k.frame != *k.sel_frame;
   const uint32_t seq = k.sel[0];
@@ -206,60 +207,38 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
   }
   __syncthreads();
 
-  // 3. codes of the selected probes into shared memory (slot order) and the
-  //    last-transmitted textures. A thread owns one code of the tile (channel,
-  //    texel) and walks the block's selected probes, all of its loads issued
-  //    before any is used.
+  // 3. the selected probes' current codes (kept by the blend) into shared
+  //    memory in slot order and into the last-transmitted textures, moved as
+  //    16-byte vectors of 8 codes
   const int n_c = sh.n_c, n_v = sh.n_v, first_c = sh.first_c, first_v = sh.first_v;
   const int* list_c = sh.list_c;
   const int* list_v = sh.list_v;
   {
-    // colour: code q = c * Tc + t; the block's threads form groups of 128,
-    // group g taking probes g, g + groups, ...
-    const int M = 3 * k.Tc;
-    constexpr int groups = SP_THREADS / 128;
-    const int g = tid >> 7;
-    for (int q = tid & 127; q < M; q += 128) {
-      const int c = q >= 2 * k.Tc ? 2 : (q >= k.Tc ? 1 : 0), t = q - c * k.Tc;
-      const int i = t / k.nc, j = t - i * k.nc;
-      const size_t pos = (size_t)(i + 1) * k.tc + j + 1;
-      uint32_t bits[SP_RANGE / groups];
-#pragma unroll
-      for (int u = 0; u < SP_RANGE / groups; ++u) {
-        const int r = g + groups * u;
-        bits[u] = r < n_c ? pv::load_state_bits(k.state_c, ((size_t)c * k.P + pb + list_c[r]) * k.sc_stride + pos,
-                                                 k.state_fmt)
-                          : 0u;
-      }
-#pragma unroll
-      for (int u = 0; u < SP_RANGE / groups; ++u) {
-        const int r = g + groups * u;
-        if (r >= n_c) continue;
-        const uint32_t code = pv::color_code_of_bits(bits[u], k.state_fmt, k.color_code);
-        sh.cc[r][q] = (uint16_t)code;
-        k.last_c[((size_t)c * k.P + pb + list_c[r]) * k.lc_stride + t] = (uint16_t)code;
-      }
+    const int vr = k.lc_stride / 8, per = 3 * vr;          // vectors per channel row, per probe
+    for (int it = tid; it < n_c * per; it += SP_THREADS) {
+      const int r = it / per, rem = it - r * per;
+      const int c = rem / vr, v = rem - c * vr;
+      const size_t row = ((size_t)c * k.P + pb + list_c[r]) * k.lc_stride;
+      const uint4 x = reinterpret_cast<const uint4*>(k.cur_c + row)[v];
+      reinterpret_cast<uint4*>(k.last_c + row)[v] = x;
+      *reinterpret_cast<uint4*>(&sh.cc[r][c * k.lc_stride + 8 * v]) = x;
     }
   }
   {
-    // visibility: code q = c * Tv + t, each thread taking every SP_THREADS-th
-    for (int q = tid; q < 2 * k.Tv; q += SP_THREADS) {
-      const int c = q >= k.Tv ? 1 : 0, t = q - c * k.Tv;
-      const int i = t / k.nv, j = t - i * k.nv;
-      const size_t pos = (size_t)(i + 1) * k.tv + j + 1;
-      uint32_t bits[SP_RANGE];
-#pragma unroll
-      for (int r = 0; r < SP_RANGE; ++r)
-        bits[r] = r < n_v ? pv::load_state_bits(k.state_v, ((size_t)c * k.P + pb + list_v[r]) * k.sv_stride + pos,
-                                                 k.state_fmt)
-                          : 0u;
-#pragma unroll
-      for (int r = 0; r < SP_RANGE; ++r) {
-        if (r >= n_v) continue;
-        const uint32_t code = pv::vis_code_of_bits(bits[r], k.state_fmt);
-        reinterpret_cast<uint16_t*>(&sh.cv[r][t])[c] = (uint16_t)code;
-        k.last_v[((size_t)c * k.P + pb + list_v[r]) * k.lv_stride + t] = (uint16_t)code;
-      }
+    // visibility: both channels of 8 texels, interleaved as R | G << 16
+    const int vr = k.lv_stride / 8;
+    for (int it = tid; it < n_v * vr; it += SP_THREADS) {
+      const int r = it / vr, v = it - r * vr;
+      const size_t row0 = ((size_t)pb + list_v[r]) * k.lv_stride, row1 = row0 + (size_t)k.P * k.lv_stride;
+      const uint4 R = reinterpret_cast<const uint4*>(k.cur_v + row0)[v];
+      const uint4 G = reinterpret_cast<const uint4*>(k.cur_v + row1)[v];
+      reinterpret_cast<uint4*>(k.last_v + row0)[v] = R;
+      reinterpret_cast<uint4*>(k.last_v + row1)[v] = G;
+      uint4* dst = reinterpret_cast<uint4*>(&sh.cv[r][8 * v]);
+      dst[0] = make_uint4(__byte_perm(R.x, G.x, 0x5410), __byte_perm(R.x, G.x, 0x7632), __byte_perm(R.y, G.y, 0x5410),
+                          __byte_perm(R.y, G.y, 0x7632));
+      dst[1] = make_uint4(__byte_perm(R.z, G.z, 0x5410), __byte_perm(R.z, G.z, 0x7632), __byte_perm(R.w, G.w, 0x5410),
+                          __byte_perm(R.w, G.w, 0x7632));
     }
   }
   if (tid < n_c) {
@@ -380,6 +359,8 @@ __global__ void __launch_bounds__(256) k_recompute_flags(pv_dev k) {
     const uint32_t code = vis ? pv::vis_code_of(st, at, k.state_fmt)
                               : pv::color_code_of(st, at, k.state_fmt, k.color_code);
     f |= code != last[t];
+    if (k.cur_c)
+      (vis ? k.cur_v : k.cur_c)[((size_t)ch * k.P + p) * (vis ? k.lv_stride : k.lc_stride) + t] = (uint16_t)code;
   }
   if (f) atomicOr(&k.chg[(vis ? k.chg_words : 0) + (p >> 5)], 1u << (p & 31));
 }

@@ -111,11 +111,14 @@ def test_config4_twelve_volumes_one_step_equals_volume_by_volume():
 def test_batch_tune_keeps_state():
     pv = H.lib()
     vols = [pv.ProbeVolume(s) for s in SMALL]
+    alone = [pv.ProbeVolume(s) for s in SMALL]
     batch = pv.ProbeBatch(vols)
     streams = _streams(SMALL, 3)
     dev, _ = _inputs(streams, 0)
     args = ([x[0] for x in dev], [x[1] for x in dev], [x[2] for x in dev])
     batch.update(*args)
+    for v, (r, d, q) in zip(alone, dev):
+        v.update(r, d, q)
     torch.cuda.synchronize()
     before = [H.gpu_state(v) for v in vols]
     np_ = batch.tune(*args, reps=2)
@@ -126,6 +129,12 @@ def test_batch_tune_keeps_state():
         for x, y in zip(b[:4], a[:4]):
             np.testing.assert_array_equal(x, y)
         assert b[4] == a[4]
+    # the frame selected after tuning is the one of the update before it
+    frames = batch.select_and_pack()
+    for va, vb, fb in zip(alone, vols, frames):
+        ga, gb = H.gpu_frame(va, va.select_and_pack()), H.gpu_frame(vb, fb)
+        for key in ga:
+            np.testing.assert_array_equal(np.asarray(ga[key]), np.asarray(gb[key]), err_msg=key)
     batch.close()
 
 
