@@ -268,7 +268,14 @@ def time_form(spec, steps, warmup, seed):
 
 
 def time_e2e(spec, steps, seed):
-    """Host buffers through the C ABI: H2D of the frame's rays and D2H of the packed frame."""
+    """Host buffers through the C ABI, every step: H2D of the frame's rays from pinned memory
+    and D2H of the packed frame (planes, index buffers, counts) into pinned memory.
+
+    Pipelined as a streaming client runs it: frame s+1's upload (the volume's copy stream)
+    and frame s's download (its second stream) overlap the kernels, and the host waits for
+    frame s-LAG after queueing frame s (LAG = 2 keeps the upload stream busy back to back;
+    three sets of host output buffers rotate). The serial form (upload, update, select,
+    blocking download) is timed beside it."""
     import numpy as np
     import torch
     import paper_2103_05875_gb300 as pv
@@ -282,36 +289,59 @@ def time_e2e(spec, steps, seed):
         host.append((rad, dist, dirs))
     vol = pv.ProbeVolume(spec)
     info = vol.info
-    color = torch.empty((3, info.color_height, info.color_width), dtype=torch.int16).pin_memory()
-    vis = torch.empty((3, info.vis_height, info.vis_width), dtype=torch.uint8).pin_memory()
-    dc = torch.empty(vol.P, dtype=torch.int16).pin_memory()
-    dv = torch.empty(vol.P, dtype=torch.int16).pin_memory()
-    counts = np.zeros(2, dtype=np.uint32)
+
+    def outs():
+        return (torch.empty((3, info.color_height, info.color_width), dtype=torch.int16).pin_memory(),
+                torch.empty((3, info.vis_height, info.vis_width), dtype=torch.uint8).pin_memory(),
+                torch.empty(vol.P, dtype=torch.int16).pin_memory(),
+                torch.empty(vol.P, dtype=torch.int16).pin_memory(),
+                torch.zeros(2, dtype=torch.int32).pin_memory())
+    lag = 2
+    out = [outs() for _ in range(lag + 1)]
     stream = torch.cuda.current_stream()
     bi = sum(t.numel() * t.element_size() for t in host[0])
-    bo_fixed = color.numel() * 2 + vis.numel() + 8
+    bo = sum(t.numel() * t.element_size() for t in out[0])
 
-    def one(s):
-        rad, dist, dirs = host[s % 2]
-        pv.probe_update_host(vol.handle, rad, dist, dirs)
-        vol.select_and_pack()
-        pv.probe_frame_download(vol.handle, color, vis, dc, dv, counts)
-        return int(counts[0] + counts[1]) * 2
+    def pipelined(n):
+        tickets = []
+        for s in range(n):
+            pv.probe_update_host(vol.handle, *host[s % 2])
+            vol.select_and_pack()
+            tickets.append(pv.probe_frame_download_async(vol.handle, *out[s % (lag + 1)]))
+            if s >= lag:
+                pv.probe_frame_wait(vol.handle, tickets[s - lag])    # frame s-lag is on the host
+        pv.probe_frame_wait(vol.handle, tickets[-1])
 
-    for s in range(3):
-        one(s)
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    idx_bytes = 0
-    t0.record(stream)
-    for s in range(steps):
-        idx_bytes += one(s)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
+    counts = np.zeros(2, dtype=np.uint32)
+    color, vis, dc, dv, _ = out[0]
+
+    def serial(n):
+        idx = 0
+        for s in range(n):
+            pv.probe_update_host(vol.handle, *host[s % 2])
+            vol.select_and_pack()
+            pv.probe_frame_download(vol.handle, color, vis, dc, dv, counts)
+            idx += int(counts[0] + counts[1]) * 2
+        return idx
+
+    def timed(fn):
+        fn(3)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        r = fn(steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1), r
+
+    ms, _ = timed(pipelined)
+    ms_serial, idx_bytes = timed(serial)
     vol.close()
     return {"value": vol.P * steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
-            "d2h_bytes_per_step": int(bo_fixed + idx_bytes / steps), "ms_per_step": ms / steps}
+            "d2h_bytes_per_step": int(bo), "ms_per_step": ms / steps,
+            "mode": f"pipelined: uploads and downloads overlap the kernels, host waits for frame s-{lag}",
+            "serial": {"value": vol.P * steps / (ms_serial / 1e3), "ms_per_step": ms_serial / steps,
+                       "d2h_bytes_per_step": int(color.numel() * 2 + vis.numel() + 8 + idx_bytes / steps)}}
 
 
 def _graph_steps(step_fns, steps, warmup):
@@ -604,6 +634,10 @@ def run_ours(args, ws, rank, local):
         line["served"] = time_served(args.served_seconds, seed)
     if rank == 0 and ws == 1 and not args.no_e2e:
         line["e2e"] = time_e2e(wl.config2(operand_fmt=forms[0]), max(10, args.steps // 2), seed)
+        if forms[0] != "f16" and "f16" in forms:           # half the upload bytes per frame
+            e16 = time_e2e(wl.config2(operand_fmt="f16"), max(10, args.steps // 2), seed)
+            line["e2e"]["f16_operands"] = {k: e16[k] for k in ("value", "ms_per_step", "h2d_bytes_per_step",
+                                                               "d2h_bytes_per_step")}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl.config2(), seed)
     if rank == 0:

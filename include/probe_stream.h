@@ -198,19 +198,48 @@ pv_status probe_select_and_pack(pv_volume* vol, pv_frame* out, int32_t want_host
                                 void* stream);
 
 /*
- * End-to-end variants with host buffers: probe_update_host copies radiance,
- * dist and dirs (host or device, layouts as above) into volume-owned device
- * staging with cudaMemcpyAsync, then runs probe_update. probe_frame_download
- * copies the last packed frame to host buffers (any may be NULL to skip):
- * color [3][color_height][color_width] uint16, vis [3][vis_height][vis_width]
- * uint8, index_c/index_v [P] uint16 (only the first count entries written),
- * counts[2] (colour, visibility). It synchronises the stream.
+ * End-to-end variants with host buffers.
+ *
+ * probe_update_host copies radiance, dist and dirs (host or device, layouts
+ * as above) into volume-owned device staging, then runs probe_update on
+ * `stream`. The staging has two halves used in turn, filled on a copy stream
+ * of the volume's own, so the upload of frame f+1 runs while frame f is
+ * blended; the update on `stream` waits for its upload, and a half is refilled
+ * only after the blend that read it. The host buffers must stay unchanged
+ * until the work this call queued on `stream` has completed; page-locked host
+ * memory makes the copies asynchronous. Inside a stream capture the copies
+ * are queued on `stream` itself (mixing captured and uncaptured host updates
+ * of one volume needs a synchronisation between them).
+ *
+ * probe_frame_download copies the last packed frame to host buffers (any may
+ * be NULL to skip): color [3][color_height][color_width] uint16,
+ * vis [3][vis_height][vis_width] uint8, delta_c/delta_v [P] uint16 (only the
+ * first count entries written), counts[2] (colour, visibility). It
+ * synchronises the stream.
+ *
+ * probe_frame_download_async queues the same copies and returns at once with
+ * a ticket (> 0). The copies run on a second stream of the volume's, after the
+ * work queued on `stream` so far, so they overlap the next frame's weights and
+ * blend; the volume's next probe_select_and_pack (single or batched) waits for
+ * them, since it rewrites the planes in place. delta_c / delta_v receive all P
+ * entries (those past the counts are unspecified). The host buffers hold the
+ * frame once probe_frame_wait(vol, ticket) has returned. Host buffers should
+ * be page-locked (pageable ones make the copies synchronous). Returns
+ * PV_ERR_UNSUPPORTED while `stream` is being captured.
+ *
+ * probe_frame_wait blocks until the download of `ticket` has landed (it may
+ * also wait for later downloads of the volume); PV_ERR_INVALID for a ticket
+ * the volume did not issue.
  */
 pv_status probe_update_host(pv_volume* vol, const void* radiance, const void* dist,
                             const float* dirs, void* stream);
 pv_status probe_frame_download(pv_volume* vol, uint16_t* color, uint8_t* vis,
                                uint16_t* delta_c, uint16_t* delta_v, uint32_t* counts,
                                void* stream);
+pv_status probe_frame_download_async(pv_volume* vol, uint16_t* color, uint8_t* vis,
+                                     uint16_t* delta_c, uint16_t* delta_v, uint32_t* counts,
+                                     uint64_t* ticket, void* stream);
+pv_status probe_frame_wait(pv_volume* vol, uint64_t ticket);
 
 /*
  * Checkpoint / resume and test injection. Buffers are host or device, layouts

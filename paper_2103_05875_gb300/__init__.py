@@ -86,6 +86,8 @@ def _load():
         "probe_select_and_pack": (i32, [vp, C.POINTER(pv_frame), i32, vp]),
         "probe_update_host": (i32, [vp, vp, vp, vp, vp]),
         "probe_frame_download": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "probe_frame_download_async": (i32, [vp, vp, vp, vp, vp, vp, C.POINTER(u64), vp]),
+        "probe_frame_wait": (i32, [vp, u64]),
         "probe_volume_export_state": (i32, [vp, vp, vp, vp, vp, C.POINTER(u64), vp]),
         "probe_volume_import_state": (i32, [vp, vp, vp, vp, vp, u64, vp]),
         "probe_update_static": (i32, [C.POINTER(pv_desc), u64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -224,6 +226,19 @@ def probe_frame_download(vol: int, color=None, vis=None, delta_c=None, delta_v=N
                          stream=None):
     _check(lib.probe_frame_download(vol, _ptr(color), _ptr(vis), _ptr(delta_c), _ptr(delta_v),
                                     _ptr(counts), _stream(stream)), "probe_frame_download")
+
+
+def probe_frame_download_async(vol: int, color=None, vis=None, delta_c=None, delta_v=None,
+                               counts=None, stream=None) -> int:
+    t = C.c_uint64()
+    _check(lib.probe_frame_download_async(vol, _ptr(color), _ptr(vis), _ptr(delta_c), _ptr(delta_v),
+                                          _ptr(counts), C.byref(t), _stream(stream)),
+           "probe_frame_download_async")
+    return t.value
+
+
+def probe_frame_wait(vol: int, ticket: int):
+    _check(lib.probe_frame_wait(vol, ticket), "probe_frame_wait")
 
 
 def probe_volume_export_state(vol: int, tiles_c, tiles_v, last_c, last_v, stream=None) -> int:

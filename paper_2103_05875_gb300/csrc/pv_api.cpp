@@ -162,6 +162,73 @@ pv_status pv_set_error(pv_status s, const char* fmt, ...) {
   return s;
 }
 
+namespace {
+
+// Streams, events and the two staging halves of the host-buffer path, made
+// on first use.
+void release_host_path(pv_volume* v) {
+  if (v->s_in) cudaStreamSynchronize(v->s_in);
+  if (v->s_out) cudaStreamSynchronize(v->s_out);
+  for (int i = 0; i < 2; ++i) {
+    if (v->ev_in_done[i]) cudaEventDestroy(v->ev_in_done[i]);
+    if (v->ev_in_free[i]) cudaEventDestroy(v->ev_in_free[i]);
+  }
+  if (v->ev_packed) cudaEventDestroy(v->ev_packed);
+  for (int i = 0; i < PV_DL_RING; ++i)
+    if (v->ev_out[i]) cudaEventDestroy(v->ev_out[i]);
+  if (v->s_in) cudaStreamDestroy(v->s_in);
+  if (v->s_out) cudaStreamDestroy(v->s_out);
+  cudaFree(v->stage);
+  v->stage = nullptr;
+  v->s_in = v->s_out = nullptr;
+  v->ev_packed = nullptr;
+  for (int i = 0; i < 2; ++i) v->ev_in_done[i] = v->ev_in_free[i] = nullptr;
+  for (int i = 0; i < PV_DL_RING; ++i) v->ev_out[i] = nullptr;
+}
+
+pv_status ensure_host_path(pv_volume* v) {
+  if (v->s_out) return PV_OK;
+  const size_t nr = (size_t)3 * v->k.P * v->k.R * v->op_bytes;
+  const size_t nd = (size_t)v->k.P * v->k.R * v->op_bytes;
+  const size_t nq = (size_t)3 * v->k.R * sizeof(float);
+  v->stage_off_dist = round_up(nr, 256);
+  v->stage_off_dirs = v->stage_off_dist + round_up(nd, 256);
+  v->stage_half = v->stage_off_dirs + round_up(nq, 256);
+  cudaError_t e = cudaMalloc((void**)&v->stage, 2 * v->stage_half);
+  if (e != cudaSuccess) {
+    v->stage = nullptr;
+    cudaGetLastError();
+    return pv_set_error(PV_ERR_OOM, "staging allocation of %zu bytes failed", 2 * v->stage_half);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->s_in, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&v->ev_in_done[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->ev_in_free[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->ev_packed, cudaEventDisableTiming);
+  for (int i = 0; i < PV_DL_RING && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&v->ev_out[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->s_out, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    release_host_path(v);
+    return cuda_fail(e, "host-buffer path setup");
+  }
+  return PV_OK;
+}
+
+bool is_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
+
+// Makes `st` wait for the volume's last queued frame download, which reads
+// the planes and index buffers the next select rewrites.
+void pv_wait_downloads(pv_volume* v, cudaStream_t st) {
+  if (v->dl_seq > 0) cudaStreamWaitEvent(st, v->ev_out[(v->dl_seq - 1) % PV_DL_RING], 0);
+}
+
 extern "C" {
 
 const char* pv_status_string(pv_status s) {
@@ -290,9 +357,7 @@ pv_status probe_volume_destroy(pv_volume* v) {
   if (!v) return PV_OK;
   DeviceGuard g(v->device);
   pv_tc_plan_destroy(v);
-  cudaFree(v->stage_rad);
-  cudaFree(v->stage_dist);
-  cudaFree(v->stage_dirs);
+  release_host_path(v);
   cudaFreeHost(v->host_counts);
   cudaFree(v->base);
   free(v);
@@ -353,6 +418,7 @@ pv_status probe_select_and_pack(pv_volume* v, pv_frame* out, int32_t want_host_c
   if (!v || !out) return pv_set_error(PV_ERR_INVALID, "probe_select_and_pack: NULL argument");
   DeviceGuard g(v->device);
   cudaStream_t st = as_stream(stream);
+  pv_wait_downloads(v, st);
   cudaError_t e = pv_launch_select_pack(v->k, st);
   if (e != cudaSuccess) return cuda_fail(e, "select/pack kernel");
   out->color_planes = v->k.planes_c;
@@ -386,25 +452,34 @@ pv_status probe_update_host(pv_volume* v, const void* rad, const void* dist, con
   if (!v || !rad || !dist || !dirs)
     return pv_set_error(PV_ERR_INVALID, "probe_update_host: NULL argument");
   DeviceGuard g(v->device);
+  pv_status s = ensure_host_path(v);
+  if (s != PV_OK) return s;
   const size_t nr = (size_t)3 * v->k.P * v->k.R * v->op_bytes;
   const size_t nd = (size_t)v->k.P * v->k.R * v->op_bytes;
   const size_t nq = (size_t)3 * v->k.R * sizeof(float);
-  cudaError_t e = cudaSuccess;
-  if (!v->stage_rad) {
-    e = cudaMalloc(&v->stage_rad, nr);
-    if (e == cudaSuccess) e = cudaMalloc(&v->stage_dist, nd);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v->stage_dirs, nq);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return pv_set_error(PV_ERR_OOM, "staging allocation failed: %s", cudaGetErrorString(e));
-    }
-  }
   cudaStream_t st = as_stream(stream);
-  e = cudaMemcpyAsync(v->stage_rad, rad, nr, cudaMemcpyDefault, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(v->stage_dist, dist, nd, cudaMemcpyDefault, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(v->stage_dirs, dirs, nq, cudaMemcpyDefault, st);
+  // inside a capture the copies join the captured stream itself
+  const bool cap = is_capturing(st);
+  const int half = v->stage_next;
+  v->stage_next ^= 1;
+  char* sr = v->stage + (size_t)half * v->stage_half;
+  char* sd = sr + v->stage_off_dist;
+  float* sq = (float*)(sr + v->stage_off_dirs);
+  cudaStream_t cs = cap ? st : v->s_in;
+  cudaError_t e = cap ? cudaSuccess : cudaStreamWaitEvent(cs, v->ev_in_free[half], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sr, rad, nr, cudaMemcpyDefault, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sd, dist, nd, cudaMemcpyDefault, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sq, dirs, nq, cudaMemcpyDefault, cs);
+  if (e == cudaSuccess && !cap) e = cudaEventRecord(v->ev_in_done[half], cs);
+  if (e == cudaSuccess && !cap) e = cudaStreamWaitEvent(st, v->ev_in_done[half], 0);
   if (e != cudaSuccess) return cuda_fail(e, "input upload");
-  return probe_update(v, v->stage_rad, v->stage_dist, v->stage_dirs, stream);
+  s = probe_update(v, sr, sd, sq, stream);
+  if (s != PV_OK) return s;
+  if (!cap) {
+    e = cudaEventRecord(v->ev_in_free[half], st);      // this half may be refilled after the blend
+    if (e != cudaSuccess) return cuda_fail(e, "input upload");
+  }
+  return PV_OK;
 }
 
 pv_status probe_frame_download(pv_volume* v, uint16_t* color, uint8_t* vis, uint16_t* delta_c,
@@ -433,6 +508,47 @@ pv_status probe_frame_download(pv_volume* v, uint16_t* color, uint8_t* vis, uint
     counts[0] = nc;
     counts[1] = nv;
   }
+  return PV_OK;
+}
+
+pv_status probe_frame_download_async(pv_volume* v, uint16_t* color, uint8_t* vis, uint16_t* delta_c,
+                                     uint16_t* delta_v, uint32_t* counts, uint64_t* ticket, void* stream) {
+  if (!v || !ticket) return pv_set_error(PV_ERR_INVALID, "probe_frame_download_async: NULL argument");
+  *ticket = 0;
+  DeviceGuard g(v->device);
+  cudaStream_t st = as_stream(stream);
+  if (is_capturing(st))
+    return pv_set_error(PV_ERR_UNSUPPORTED, "probe_frame_download_async: the stream is being captured");
+  pv_status s = ensure_host_path(v);
+  if (s != PV_OK) return s;
+  const pv_dev& k = v->k;
+  cudaStream_t so = v->s_out;
+  cudaError_t e = cudaEventRecord(v->ev_packed, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(so, v->ev_packed, 0);
+  if (e == cudaSuccess && counts) e = cudaMemcpyAsync(counts, k.counts, 2 * sizeof(uint32_t), cudaMemcpyDefault, so);
+  if (e == cudaSuccess && color)
+    e = cudaMemcpy2DAsync(color, (size_t)v->cwidth * 2, k.planes_c, k.cpitch, (size_t)v->cwidth * 2,
+                          (size_t)3 * k.ch, cudaMemcpyDefault, so);
+  if (e == cudaSuccess && vis)
+    e = cudaMemcpy2DAsync(vis, (size_t)k.vwidth, k.planes_v, k.vpitch, (size_t)k.vwidth, (size_t)3 * k.vh,
+                          cudaMemcpyDefault, so);
+  if (e == cudaSuccess && delta_c) e = cudaMemcpyAsync(delta_c, k.delta_c, (size_t)k.P * 2, cudaMemcpyDefault, so);
+  if (e == cudaSuccess && delta_v) e = cudaMemcpyAsync(delta_v, k.delta_v, (size_t)k.P * 2, cudaMemcpyDefault, so);
+  if (e == cudaSuccess) e = cudaEventRecord(v->ev_out[v->dl_seq % PV_DL_RING], so);
+  if (e != cudaSuccess) return cuda_fail(e, "frame download");
+  *ticket = ++v->dl_seq;
+  return PV_OK;
+}
+
+pv_status probe_frame_wait(pv_volume* v, uint64_t ticket) {
+  if (!v) return pv_set_error(PV_ERR_INVALID, "probe_frame_wait: NULL volume");
+  if (ticket == 0 || ticket > v->dl_seq)
+    return pv_set_error(PV_ERR_INVALID, "probe_frame_wait: ticket %llu was not issued", (unsigned long long)ticket);
+  DeviceGuard g(v->device);
+  // a reused event stands for a later download on the same stream, which
+  // lands after this one
+  const cudaError_t e = cudaEventSynchronize(v->ev_out[(ticket - 1) % PV_DL_RING]);
+  if (e != cudaSuccess) return cuda_fail(e, "probe_frame_wait");
   return PV_OK;
 }
 

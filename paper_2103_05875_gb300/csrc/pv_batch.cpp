@@ -145,7 +145,10 @@ pv_status probe_batch_select_and_pack(pv_batch* b, pv_frame* out, void* stream) 
   if (!b || !out) return pv_set_error(PV_ERR_INVALID, "probe_batch_select_and_pack: NULL argument");
   DeviceGuard g(b->device);
   pv_dev ks[PV_MAX_BATCH];
-  for (int i = 0; i < b->n; ++i) ks[i] = b->vols[i]->k;
+  for (int i = 0; i < b->n; ++i) {
+    ks[i] = b->vols[i]->k;
+    pv_wait_downloads(b->vols[i], as_stream(stream));
+  }
   cudaError_t e = pv_launch_select_pack_batch(ks, b->n, as_stream(stream));
   if (e != cudaSuccess) return cuda_fail(e, "batched select/pack kernel");
   for (int i = 0; i < b->n; ++i) fill_frame(b->vols[i], &out[i]);

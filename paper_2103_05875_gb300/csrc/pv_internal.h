@@ -54,6 +54,8 @@ struct pv_dev {
   int* err;                             // [1] device error word (non-zero: a bounded wait gave up)
 };
 
+constexpr int PV_DL_RING = 8;          // download events kept per volume
+
 struct pv_volume {
   pv_desc d;
   pv_dev k;
@@ -63,13 +65,23 @@ struct pv_volume {
   int cwidth;                           // colour plane width in samples
   char* base;                           // single device allocation
   size_t bytes;
-  void* stage_rad;                      // staging for probe_update_host
-  void* stage_dist;
-  float* stage_dirs;
+  // host-buffer path: two halves of input staging, each filled on s_in while
+  // the other feeds the blend, and frame downloads on s_out
+  char* stage;                          // 2 x (radiance | dist | dirs)
+  size_t stage_half, stage_off_dist, stage_off_dirs;
+  int stage_next;
+  cudaStream_t s_in, s_out;
+  cudaEvent_t ev_in_done[2], ev_in_free[2], ev_packed;
+  cudaEvent_t ev_out[PV_DL_RING];       // download tickets, reused round robin
+  unsigned long long dl_seq;            // downloads queued so far
   uint32_t* host_counts;                // pinned [4]
   unsigned long long frame;             // host mirror of the frame counter
   void* tc_plan;                        // tensor-core kernel plan (tensor maps), or NULL
 };
+
+// Makes `st` wait for the volume's last queued frame download (the next
+// select rewrites what it reads).
+void pv_wait_downloads(pv_volume* v, cudaStream_t st);
 
 // Byte offset of ray r of image row `row` in one plane of w_op. Each chunk of
 // w_kc rays is a w_rows x w_rb tile with the 16-byte units of a row XORed by

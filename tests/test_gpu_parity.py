@@ -252,6 +252,61 @@ def test_host_buffer_path_matches_device_path():
     b.close()
 
 
+def test_pipelined_host_path_matches_device_path():
+    """Uploads on the volume's copy stream into alternating staging halves and downloads
+    queued on its second stream, frame f+1 queued before frame f is waited for: every
+    frame must equal the device-buffer path's, the next select waiting for the download
+    of the planes it rewrites."""
+    spec = _spec(nx=6, ny=4, nz=5, rays=64, state_fmt="f16")
+    pv = H.lib()
+    a = pv.ProbeVolume(spec)
+    b = pv.ProbeVolume(spec)
+    fs = wl.FrameStream(spec, 9)
+    info = a.info
+    frames = 6
+    host_in, expect = [], []
+    for f in range(frames):
+        (rad, dist, dirs), _ = H.device_inputs(fs, f)
+        host_in.append((rad.cpu().pin_memory(), dist.cpu().pin_memory(), dirs.cpu().pin_memory()))
+        a.update(rad, dist, dirs)
+        expect.append(H.gpu_frame(a, a.select_and_pack(want_host_counts=True)))
+
+    def bufs():
+        return (torch.zeros((3, info.color_height, info.color_width), dtype=torch.int16).pin_memory(),
+                torch.zeros((3, info.vis_height, info.vis_width), dtype=torch.uint8).pin_memory(),
+                torch.zeros(spec.probes, dtype=torch.int16).pin_memory(),
+                torch.zeros(spec.probes, dtype=torch.int16).pin_memory(),
+                torch.zeros(2, dtype=torch.int32).pin_memory())
+    out = [bufs(), bufs()]
+
+    def check(f):
+        color, vis, dc, dv, counts = out[f % 2]
+        g = expect[f]
+        nc, nv = int(counts[0]), int(counts[1])
+        assert nc == g["count_c"] and nv == g["count_v"]
+        np.testing.assert_array_equal(color.numpy().view(np.uint16), g["planes_c"])
+        np.testing.assert_array_equal(vis.numpy(), g["planes_v"])
+        np.testing.assert_array_equal(dc.numpy().view(np.uint16)[:nc], g["delta_c"])
+        np.testing.assert_array_equal(dv.numpy().view(np.uint16)[:nv], g["delta_v"])
+
+    tickets = []
+    for f in range(frames):
+        pv.probe_update_host(b.handle, *host_in[f])
+        b.select_and_pack()
+        tickets.append(pv.probe_frame_download_async(b.handle, *out[f % 2]))
+        if f:
+            pv.probe_frame_wait(b.handle, tickets[f - 1])
+            check(f - 1)
+    pv.probe_frame_wait(b.handle, tickets[-1])
+    check(frames - 1)
+    assert tickets == list(range(1, frames + 1))
+    with pytest.raises(pv.PVError) as e:
+        pv.probe_frame_wait(b.handle, frames + 1)
+    assert e.value.status == -1
+    a.close()
+    b.close()
+
+
 def test_invalid_arguments_return_errors():
     pv = H.lib()
     with pytest.raises(pv.PVError) as e:
