@@ -327,6 +327,8 @@ pv_status probe_volume_create(const pv_desc* d, pv_volume** out) {
   k.w_rows = L.w_rows; k.w_rb = L.w_rb; k.w_kc = L.w_kc; k.w_vb = L.w_vb; k.w_chunks = L.w_chunks;
   k.sc_stride = L.sc_stride; k.sv_stride = L.sv_stride;
   k.lc_stride = L.lc_stride; k.lv_stride = L.lv_stride;
+  k.rcp_nc = pv_rcp31((uint32_t)L.nc); k.rcp_nv = pv_rcp31((uint32_t)L.nv);
+  k.rcp_vc = pv_rcp31((uint32_t)L.lc_stride / 8); k.rcp_vv = pv_rcp31((uint32_t)L.lv_stride / 8);
   k.err = (int*)(b + L.off_err);
 
   // zero everything, then mark every probe "never sent"

@@ -51,6 +51,9 @@ struct pv_dev {
                                         // chunks per plane
   int sc_stride, sv_stride;             // elements per probe tile in state memory (16-byte multiple)
   int lc_stride, lv_stride;             // codes per probe in the last-transmitted arrays (multiple of 8)
+  // ceil(2^31 / d) for d = n_c, n_v, lc_stride / 8, lv_stride / 8: the
+  // select kernel divides small indices by them with one multiply (pv_rcp31)
+  uint32_t rcp_nc, rcp_nv, rcp_vc, rcp_vv;
   int* err;                             // [1] device error word (non-zero: a bounded wait gave up)
 };
 
@@ -78,6 +81,10 @@ struct pv_volume {
   unsigned long long frame;             // host mirror of the frame counter
   void* tc_plan;                        // tensor-core kernel plan (tensor maps), or NULL
 };
+
+// ceil(2^31 / d); x / d == umulhi(2x, ceil(2^31 / d)) for 0 <= x < 2^16 and
+// 1 <= d <= 2^15 (the rounding excess x * (m - 2^31 / d) / 2^31 stays below 1/d).
+inline uint32_t pv_rcp31(uint32_t d) { return (uint32_t)(((1ull << 31) + d - 1) / d); }
 
 // Makes `st` wait for the volume's last queued frame download (the next
 // select rewrites what it reads).

@@ -3,26 +3,28 @@
 // recomputation used after a state import.
 //
 // Selection: the blend raises bit p of the colour (visibility) mask when a
-// transmitted code of probe p differs from its last-transmitted code; slots
-// are assigned in ascending probe id. Each block reads both masks (P/8 bytes
-// each) and reduces them, so it knows its probes' slots, the last selected
-// probe before its range (for the delta code) and the totals without any
-// grid-wide synchronisation. It then packs its own contiguous probe range, one
-// warp per probe:
-//   colour: the 10-bit codes of the interior go to planes Y=R, U=G, V=B at
+// transmitted code of probe p differs from its last-transmitted code, and
+// keeps every probe's current codes; slots are assigned in ascending probe
+// id. A block owns SP_RANGE consecutive probes. It first starts asynchronous
+// copies of its probes' current codes into shared memory; meanwhile its first
+// warp reads both masks (P/8 bytes each) and reduces them, so the block knows
+// its probes' slots, the last selected probe before its range (for the delta
+// code) and the totals without any grid-wide synchronisation. After one
+// barrier it writes, for its selected probes:
+//   the last-transmitted codes (16-byte vectors from the staged codes);
+//   the index buffer entries and deltas (d0 = id0, dk = id_k - id_(k-1));
+//   colour: the 10-bit codes of the interior to planes Y=R, U=G, V=B at
 //           block (k / B_w, k % B_w) as 16-bit samples (code << 6 unless
-//           color_lsb), and to the last-transmitted texture;
+//           color_lsb);
 //   visibility: per atlas row each texel's bytes (R.lo, R.hi, G.lo, G.hi)
 //           continue the row's byte stream; byte s goes to plane s mod 3,
-//           column s div 3 (the paper's YUVY / UVYU / VYUV pattern). Byte
-//           stores, because neighbouring slots share plane words.
-// Each block writes its probes' index-buffer entries and deltas
-// (d0 = id0, dk = id_k - id_(k-1)), and clears its share of the slots that
-// held a probe last frame but are empty now (slots beyond both counts are
-// already zero). The masks count once per update: the kernel compares the
-// frame counter with the frame of the previous select, so a second select
-// without a new update selects nothing. The last block to finish advances the
-// select sequence, which double-buffers the previous counts.
+//           column s div 3 (the paper's YUVY / UVYU / VYUV pattern).
+// It also clears its share of the slots that held a probe last frame but are
+// empty now (slots beyond both counts are already zero). The masks count once
+// per update: the kernel compares the frame counter with the frame of the
+// previous select, so a second select without a new update selects nothing.
+// The last block to finish advances the select sequence, which
+// double-buffers the previous counts.
 #include "pv_codes.cuh"
 #include "pv_internal.h"
 
@@ -31,33 +33,43 @@ namespace {
 // 256 threads and 8 probes per block keep a 16^3 volume's 512 blocks resident
 // in one wave (several blocks per SM)
 constexpr int SP_THREADS = 256;
-constexpr int SP_WARPS = SP_THREADS / 32;
 constexpr int SP_RANGE = 8;              // probes per block: their codes are staged in shared memory
 constexpr int SP_MAX_T = PV_MAX_INTERIOR * PV_MAX_INTERIOR;
 
 struct SpShared {
-  uint16_t cc[SP_RANGE][3 * SP_MAX_T];   // colour codes of the block's selected probes, slot order,
-                                         // channel rows lc_stride apart
-  uint32_t cv[SP_RANGE][SP_MAX_T];       // visibility codes, slot order: R | G << 16 per texel
+  // current codes of the block's probes (local index), channel rows lc_stride
+  // (colour) and lv_stride (visibility R then G) apart
+  uint16_t cc[SP_RANGE][3 * SP_MAX_T];
+  uint16_t cv[SP_RANGE][2 * SP_MAX_T];
   int slot_c[SP_RANGE], slot_v[SP_RANGE];
   uint16_t prev_c[SP_RANGE], prev_v[SP_RANGE];
   int list_c[SP_RANGE], list_v[SP_RANGE];  // the block's selected probes (local index), slot order
   int n_c, n_v, first_c, first_v;          // how many, and the slot of the first
-  int red[3 * SP_WARPS];
+  int tot_c, tot_v, prev_cnt_c, prev_cnt_v;
+  uint32_t seq;
 };
 
-// Colour samples of slots [a, b) (all in one block row) from staged codes
-// cc[q0 + slot - a] (zero when `clear`). A thread owns one column of the run
-// (one division) and writes it down all 3 * n_c rows; consecutive threads
-// write consecutive 16-bit samples.
+// x / d for 0 <= x < 2^16, with m = ceil(2^31 / d) (pv_rcp31)
+__device__ __forceinline__ int fdiv(int x, uint32_t m) { return (int)__umulhi((uint32_t)x << 1, m); }
+
+// ceil(2^31 / d) for run lengths d = 1..SP_RANGE
+__constant__ uint32_t c_rcp_run[SP_RANGE + 1] = {0u,          0x80000000u, 0x40000000u, 0x2AAAAAABu, 0x20000000u,
+                                                 0x1999999Au, 0x15555556u, 0x12492493u, 0x10000000u};
+
+// Colour samples of slots [a, b) (all in one block row) from the staged codes
+// of the block's selected probe list_c[q0 + slot - a] (zero when `clear`).
+// Thread tid = (g * cnt + so) * n + j owns column j of slot so and writes it
+// down rows g, g + groups, ... of the 3 * n_c rows; consecutive threads write
+// consecutive 16-bit samples.
 __device__ __forceinline__ void write_color_run(const pv_dev& k, const SpShared& sh, int a, int b, int q0, bool clear) {
-  const int n = k.nc, by = a / k.bw, bx0 = a % k.bw;
-  const int cols = (b - a) * n;
-  const int groups = SP_THREADS / cols > 0 ? SP_THREADS / cols : 1;   // threads per column
-  const int x = threadIdx.x % cols, g = threadIdx.x / cols;
+  const int n = k.nc, cnt = b - a;
+  const int by = a / k.bw, bx0 = a - by * k.bw;
+  const int t2 = fdiv(threadIdx.x, k.rcp_nc), j = threadIdx.x - t2 * n;
+  const int g = fdiv(t2, c_rcp_run[cnt]), so = t2 - g * cnt;
+  const int groups = fdiv(fdiv(SP_THREADS, k.rcp_nc), c_rcp_run[cnt]);   // = SP_THREADS / (cnt * n)
   if (g >= groups) return;
-  const int so = x / n, j = x - so * n;
-  const uint16_t* src = sh.cc[q0 + so] + j;
+  const int x = so * n + j;
+  const uint16_t* src = sh.cc[clear ? 0 : sh.list_c[q0 + so]] + j;
   uint8_t* base = reinterpret_cast<uint8_t*>(k.planes_c) + ((size_t)by * n) * k.cpitch + ((size_t)bx0 * n + x) * 2;
   for (int row = g; row < 3 * n; row += groups) {      // row = c * n + i
     const int c = row >= 2 * n ? 2 : (row >= n ? 1 : 0), i = row - c * n;
@@ -76,21 +88,23 @@ __device__ __forceinline__ void write_color_run(const pv_dev& k, const SpShared&
 // bytes with neighbouring slots (written by other blocks) and are written byte
 // by byte, only where they belong to these slots.
 __device__ __forceinline__ void write_vis_run(const pv_dev& k, const SpShared& sh, int a, int b, int q0, bool clear) {
-  const int n = k.nv, by = a / k.bw, bx0 = a % k.bw;
+  const int n = k.nv, by = a / k.bw, bx0 = a - by * k.bw;
   const int s_lo = 4 * n * bx0, s_hi = 4 * n * (bx0 + (b - a));   // stream bytes [s_lo, s_hi)
   const int w_lo = s_lo / 12, w_hi = (s_hi - 1) / 12;             // chunks touched
   const int nw = w_hi - w_lo + 1;
+  const uint32_t rcp_nw = (0x80000000u + (uint32_t)nw - 1u) / (uint32_t)nw;
   const size_t plane = (size_t)k.vh * k.vpitch;
   for (int q = threadIdx.x; q < n * nw; q += SP_THREADS) {
-    const int i = q / nw, w = w_lo + (q - i * nw);
+    const int i = fdiv(q, rcp_nw), w = w_lo + (q - i * nw);
     uint32_t t3[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {                                 // texels 3w, 3w+1, 3w+2 of the atlas row
       const int X = 3 * w + e - n * bx0;                          // texel column within the run
       t3[e] = 0u;
       if (!clear && X >= 0 && X < n * (b - a)) {
-        const int so = X / n, j = X - so * n;
-        t3[e] = sh.cv[q0 + so][i * n + j];
+        const int so = fdiv(X, k.rcp_nv), j = X - so * n;
+        const uint16_t* src = sh.cv[sh.list_v[q0 + so]] + i * n + j;
+        t3[e] = (uint32_t)src[0] | (uint32_t)src[k.lv_stride] << 16;
       }
     }
     const uint32_t w0 = __byte_perm(__byte_perm(t3[0], t3[1], 0x0630), t3[2], 0x5210);
@@ -126,20 +140,9 @@ __device__ __forceinline__ void for_runs(const pv_dev& k, int s0, int s1, F fn) 
   }
 }
 
-// Block-wide sums (and maxima) of three values over all threads.
-__device__ __forceinline__ void block_reduce3(int& a, int& b, int& c, int* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
-  }
-  if (lane == 0) { sh[3 * wid] = a; sh[3 * wid + 1] = b; sh[3 * wid + 2] = c; }
-  __syncthreads();
-  a = 0; b = 0; c = -1;
-  for (int w = 0; w < SP_WARPS; ++w) { a += sh[3 * w]; b += sh[3 * w + 1]; c = max(c, sh[3 * w + 2]); }
-  __syncthreads();
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
 }
 
 // Block `bid` of the `nblocks` blocks that select and pack volume k; block
@@ -147,19 +150,34 @@ __device__ __forceinline__ void block_reduce3(int& a, int& b, int& c, int* sh) {
 __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int nblocks) {
   __shared__ __align__(16) SpShared sh;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const bool fresh = *k.frame != *k.sel_frame;
-  const uint32_t seq = k.sel[0];
-  const uint32_t par = seq & 1u;
-  const int prev_cnt_c = (int)k.sel[2 + 2 * (par ^ 1u)], prev_cnt_v = (int)k.sel[3 + 2 * (par ^ 1u)];
   const int pb = bid * SP_RANGE, pe = min(k.P, pb + SP_RANGE);
   const int W = k.chg_words, wb = pb >> 5;
+  const int vc = k.lc_stride / 8, vv = k.lv_stride / 8;    // 16-byte vectors per channel row
 
+  // 0. copies of the block's current codes into shared memory, in flight
+  //    while the masks are read (every probe of the range: most are selected)
+  for (int it = tid; it < (pe - pb) * 3 * vc; it += SP_THREADS) {
+    const int t = fdiv(it, k.rcp_vc), v = it - t * vc, q = t / 3, c = t - 3 * q;
+    cp_async16(&sh.cc[q][c * k.lc_stride + 8 * v], k.cur_c + ((size_t)c * k.P + pb + q) * k.lc_stride + 8 * v);
+  }
+  for (int it = tid; it < (pe - pb) * 2 * vv; it += SP_THREADS) {
+    const int t = fdiv(it, k.rcp_vv), v = it - t * vv, q = t >> 1, c = t & 1;
+    cp_async16(&sh.cv[q][c * k.lv_stride + 8 * v], k.cur_v + ((size_t)c * k.P + pb + q) * k.lv_stride + 8 * v);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 
-  // 1. totals, selected probes before this block's first word, last of them
-  int tot_c = 0, tot_v = 0, dummy = -1;
-  int bef_c = 0, bef_v = 0, last_c = -1, last_v = -1;
-  if (fresh) {
-    for (int w = tid; w < W; w += SP_THREADS) {
+  // 1. first warp: select state, totals, selected probes before this block's
+  //    word and the last of them, then the slots of the block's probes (lane
+  //    = bit of the block's word, rank from a prefix count of the word). All
+  //    loads are issued before any is used.
+  if (wid == 0) {
+    const unsigned long long fr = *k.frame, sf = *k.sel_frame;
+    const uint32_t seq = k.sel[0];
+    const uint32_t cnt2 = k.sel[2], cnt3 = k.sel[3], cnt4 = k.sel[4], cnt5 = k.sel[5];
+    const uint32_t own_c = k.chg[wb], own_v = k.chg[W + wb];
+    int tot_c = 0, tot_v = 0, bef_c = 0, bef_v = 0, last_c = -1, last_v = -1;
+#pragma unroll 4
+    for (int w = lane; w < W; w += 32) {
       const uint32_t mc = k.chg[w], mv = k.chg[W + w];
       tot_c += __popc(mc);
       tot_v += __popc(mv);
@@ -170,17 +188,18 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
         if (mv) last_v = max(last_v, 32 * w + 31 - __clz(mv));
       }
     }
-  }
-  block_reduce3(tot_c, tot_v, dummy, sh.red);
-  int zero_c = 0;
-  block_reduce3(bef_c, zero_c, last_c, sh.red);
-  int zero_v = 0;
-  block_reduce3(bef_v, zero_v, last_v, sh.red);
-
-  // 2. slots of this block's probes: lane = bit of the block's word; the
-  //    selected probes before a lane come from a prefix count of the word
-  if (wid == 0) {
-    const uint32_t mc = (fresh && pb < pe) ? k.chg[wb] : 0u, mv = (fresh && pb < pe) ? k.chg[W + wb] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tot_c += __shfl_xor_sync(0xffffffffu, tot_c, o);
+      tot_v += __shfl_xor_sync(0xffffffffu, tot_v, o);
+      bef_c += __shfl_xor_sync(0xffffffffu, bef_c, o);
+      bef_v += __shfl_xor_sync(0xffffffffu, bef_v, o);
+      last_c = max(last_c, __shfl_xor_sync(0xffffffffu, last_c, o));
+      last_v = max(last_v, __shfl_xor_sync(0xffffffffu, last_v, o));
+    }
+    const bool fresh = fr != sf;                   // masks not yet consumed by a select
+    if (!fresh) tot_c = tot_v = bef_c = bef_v = 0, last_c = last_v = -1;
+    const uint32_t mc = (fresh && pb < pe) ? own_c : 0u, mv = (fresh && pb < pe) ? own_v : 0u;
     const uint32_t below = (1u << lane) - 1u;
     const int p = 32 * wb + lane;
     const bool in = p >= pb && p < pe;
@@ -194,6 +213,12 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
     if (lane == 0) {
       sh.n_c = __popc(bal_c);
       sh.n_v = __popc(bal_v);
+      sh.tot_c = tot_c;
+      sh.tot_v = tot_v;
+      const bool odd = (seq & 1u) != 0u;           // previous counts: the other parity's pair
+      sh.prev_cnt_c = (int)(odd ? cnt2 : cnt4);
+      sh.prev_cnt_v = (int)(odd ? cnt3 : cnt5);
+      sh.seq = seq;
     }
     if (in) {
       const uint32_t bc = mc & below, bv = mv & below;
@@ -205,42 +230,26 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
       sh.prev_v[p - pb] = (uint16_t)(lv < 0 ? 0 : lv);
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-
-  // 3. the selected probes' current codes (kept by the blend) into shared
-  //    memory in slot order and into the last-transmitted textures, moved as
-  //    16-byte vectors of 8 codes
   const int n_c = sh.n_c, n_v = sh.n_v, first_c = sh.first_c, first_v = sh.first_v;
+  const int tot_c = sh.tot_c, tot_v = sh.tot_v, prev_cnt_c = sh.prev_cnt_c, prev_cnt_v = sh.prev_cnt_v;
+  const uint32_t seq = sh.seq, par = seq & 1u;
   const int* list_c = sh.list_c;
   const int* list_v = sh.list_v;
-  {
-    const int vr = k.lc_stride / 8, per = 3 * vr;          // vectors per channel row, per probe
-    for (int it = tid; it < n_c * per; it += SP_THREADS) {
-      const int r = it / per, rem = it - r * per;
-      const int c = rem / vr, v = rem - c * vr;
-      const size_t row = ((size_t)c * k.P + pb + list_c[r]) * k.lc_stride;
-      const uint4 x = reinterpret_cast<const uint4*>(k.cur_c + row)[v];
-      reinterpret_cast<uint4*>(k.last_c + row)[v] = x;
-      *reinterpret_cast<uint4*>(&sh.cc[r][c * k.lc_stride + 8 * v]) = x;
-    }
+
+  // 2. the selected probes' codes into the last-transmitted textures
+  for (int it = tid; it < n_c * 3 * vc; it += SP_THREADS) {
+    const int t = fdiv(it, k.rcp_vc), v = it - t * vc, r = t / 3, c = t - 3 * r, q = list_c[r];
+    reinterpret_cast<uint4*>(k.last_c + ((size_t)c * k.P + pb + q) * k.lc_stride)[v] =
+        *reinterpret_cast<const uint4*>(&sh.cc[q][c * k.lc_stride + 8 * v]);
   }
-  {
-    // visibility: both channels of 8 texels, interleaved as R | G << 16
-    const int vr = k.lv_stride / 8;
-    for (int it = tid; it < n_v * vr; it += SP_THREADS) {
-      const int r = it / vr, v = it - r * vr;
-      const size_t row0 = ((size_t)pb + list_v[r]) * k.lv_stride, row1 = row0 + (size_t)k.P * k.lv_stride;
-      const uint4 R = reinterpret_cast<const uint4*>(k.cur_v + row0)[v];
-      const uint4 G = reinterpret_cast<const uint4*>(k.cur_v + row1)[v];
-      reinterpret_cast<uint4*>(k.last_v + row0)[v] = R;
-      reinterpret_cast<uint4*>(k.last_v + row1)[v] = G;
-      uint4* dst = reinterpret_cast<uint4*>(&sh.cv[r][8 * v]);
-      dst[0] = make_uint4(__byte_perm(R.x, G.x, 0x5410), __byte_perm(R.x, G.x, 0x7632), __byte_perm(R.y, G.y, 0x5410),
-                          __byte_perm(R.y, G.y, 0x7632));
-      dst[1] = make_uint4(__byte_perm(R.z, G.z, 0x5410), __byte_perm(R.z, G.z, 0x7632), __byte_perm(R.w, G.w, 0x5410),
-                          __byte_perm(R.w, G.w, 0x7632));
-    }
+  for (int it = tid; it < n_v * 2 * vv; it += SP_THREADS) {
+    const int t = fdiv(it, k.rcp_vv), v = it - t * vv, r = t >> 1, c = t & 1, q = list_v[r];
+    reinterpret_cast<uint4*>(k.last_v + ((size_t)c * k.P + pb + q) * k.lv_stride)[v] =
+        *reinterpret_cast<const uint4*>(&sh.cv[q][c * k.lv_stride + 8 * v]);
   }
+  // 3. index buffers
   if (tid < n_c) {
     const int lp = list_c[tid], sc = sh.slot_c[lp];
     k.idx_c[sc] = (uint16_t)(pb + lp);
@@ -251,7 +260,6 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
     k.idx_v[sv] = (uint16_t)(pb + lp);
     k.delta_v[sv] = (uint16_t)(pb + lp - sh.prev_v[lp]);
   }
-  __syncthreads();
 
   // 4. the block's slots into the planes, one block row at a time
   if (n_c > 0)

@@ -71,3 +71,17 @@ def test_host_only_entry_points(built_lib):
         pv.probe_volume_bytes(pv.make_desc(wl.config2(), hysteresis=1.5))
     assert e.value.status == -1
     assert pv.lib.pv_status_string(-5) == b"PV_ERR_TIMEOUT"
+
+
+def test_select_kernel_reciprocal_division_is_exact():
+    """The select kernel divides small indices (x < 2^16) by d <= 2^15 as umulhi(2x, ceil(2^31/d));
+    the run-length table in its source must hold ceil(2^31/d) for d = 1..8."""
+    import re
+    x = np.arange(1 << 16, dtype=np.uint64)
+    for d in list(range(1, 257)) + [4097, 12345, 32767, 1 << 15]:
+        m = ((1 << 31) + d - 1) // d
+        np.testing.assert_array_equal(((2 * x) * m) >> 32, x // d, err_msg=f"d={d}")
+    src = open(os.path.join(ROOT, "paper_2103_05875_gb300", "csrc", "pv_select_pack.cu")).read()
+    table = re.search(r"c_rcp_run\[[^\]]*\]\s*=\s*\{([^}]*)\}", src).group(1)
+    vals = [int(v.strip().rstrip("u"), 16) for v in table.split(",")]
+    assert vals[1:] == [((1 << 31) + d - 1) // d for d in range(1, len(vals))]
