@@ -23,8 +23,9 @@
 // empty now (slots beyond both counts are already zero). The masks count once
 // per update: the kernel compares the frame counter with the frame of the
 // previous select, so a second select without a new update selects nothing.
-// The last block to finish advances the select sequence, which
-// double-buffers the previous counts.
+// The last block to have read the select state advances the select sequence,
+// which double-buffers the previous counts; the next select sees it, since a
+// kernel waits for its predecessors to complete before reading.
 #include "pv_codes.cuh"
 #include "pv_internal.h"
 
@@ -237,6 +238,17 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
   const uint32_t seq = sh.seq, par = seq & 1u;
   const int* list_c = sh.list_c;
   const int* list_v = sh.list_v;
+  // every thread of the block has what it needs of the select state (the
+  // sequence, the previous counts, the frame of the last select): the last
+  // block to get here advances it for the next select
+  if (tid == 0) {
+    const uint32_t ticket = atomicAdd(&k.sel[1], 1u);
+    if (ticket == (uint32_t)nblocks - 1) {
+      k.sel[1] = 0;
+      k.sel[0] = seq + 1u;
+      *k.sel_frame = *k.frame;
+    }
+  }
 
   // 2. the selected probes' codes into the last-transmitted textures
   for (int it = tid; it < n_c * 3 * vc; it += SP_THREADS) {
@@ -271,23 +283,13 @@ __device__ __forceinline__ void select_pack_block(const pv_dev& k, int bid, int 
     for_runs(k, a, min(prev_cnt_c, a + SP_RANGE), [&](int x, int y, int q0) { write_color_run(k, sh, x, y, q0, true); });
   for (int a = tot_v + bid * SP_RANGE; a < prev_cnt_v; a += nblocks * SP_RANGE)
     for_runs(k, a, min(prev_cnt_v, a + SP_RANGE), [&](int x, int y, int q0) { write_vis_run(k, sh, x, y, q0, true); });
-  // 6. counts, and the select sequence once every block is done
+  // 6. counts, into this select's parity slot (the previous counts, read
+  //    above by every block, sit in the other one)
   if (bid == 0 && tid == 0) {
     k.counts[0] = (uint32_t)tot_c;
     k.counts[1] = (uint32_t)tot_v;
     k.sel[2 + 2 * par] = (uint32_t)tot_c;
     k.sel[3 + 2 * par] = (uint32_t)tot_v;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const uint32_t ticket = atomicAdd(&k.sel[1], 1u);
-    if (ticket == (uint32_t)nblocks - 1) {
-      k.sel[1] = 0;
-      k.sel[0] = seq + 1u;
-      *k.sel_frame = *k.frame;
-      __threadfence();
-    }
   }
 }
 
