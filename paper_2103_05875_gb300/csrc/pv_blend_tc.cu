@@ -99,6 +99,8 @@ struct TcParams {
   uint32_t tidesc[4];
   int off_a_lo, off_w, off_w_lo, stage_bytes;
   int off_state, off_last, off_rsum, off_pos, off_gb, off_flags, off_bar;
+  int alias_stages;                      // > 0: one item per CTA, whose old texels and codes live in
+                                         // the first alias_stages stages of the ring (loaded at its end)
   int gb_c, gb_v;                        // guard-band texels per tile: 4n + 4
   uint32_t stage_tx, w_tx;               // bytes per stage: all, weight tiles only
 };
@@ -572,9 +574,12 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  // everything above ran while the previous kernel may still be running;
-  // from here on the kernel reads what it (and the kernels before it) wrote
-  pv_grid_wait();
+  // Everything above runs while the previous kernel may still be running.
+  // Each role waits for it (pv_grid_wait) just before its first read of
+  // memory a predecessor wrote: the producer before its first load, the
+  // epilogue before it reads sums, hysteresis and old tiles. The MMA issuer
+  // and the converters touch only shared memory and TMEM. Parameter reads
+  // before the wait overlap the predecessor's tail.
   int* err = k.err;
   const uint32_t crank = tp.cluster > 1 ? cluster_rank() : 0u;
   const uint16_t cmask = (uint16_t)((1u << tp.cluster) - 1u);
@@ -589,6 +594,13 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].dist) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].rad) : "memory");
       }
+      {  // the first item's parameters, fetched before the wait
+        const BlendVol& b0 = a.v[vol_of(a, (int)blockIdx.x < tp.items ? (int)blockIdx.x : tp.items - 1)];
+        asm volatile("" ::"r"(b0.nchunks), "r"(b0.item0), "r"(b0.k.P), "l"(b0.k.w_op), "r"(b0.k.w_chunks),
+                     "r"(tp.stage_tx), "r"(tp.w_tx), "r"(tp.kc), "r"(tp.crow), "r"(tp.ntiles), "r"(tp.off_w),
+                     "r"(tp.off_w_lo), "r"(tp.stages), "r"(tp.stage_bytes));
+      }
+      pv_grid_wait();
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -629,6 +641,24 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
             s = 0;
             ph ^= 1;
           }
+        }
+      }
+      // one item per CTA: its old texels and codes go into the first
+      // alias_stages stages once the MMAs that read those stages are done
+      if (tp.alias_stages > 0 && rounds > 0 && ok) {
+        const uint32_t need = (1u << tp.alias_stages) - 1u;
+        uint32_t got = 0u;
+        for (int i = 0; i < tp.stages && ok && (got & need) != need; ++i) {
+          ok = mbar_wait(&empty[s], ph ^ 1, err);
+          got |= 1u << s;
+          if (++s == tp.stages) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+        if (ok) {
+          const BlendVol& bv = a.v[vol_of(a, blockIdx.x)];
+          prefetch_item(bv.k, np, ((int)blockIdx.x - bv.item0) * np, sb, st_c, st_v, ls_c, ls_v, efull);
         }
       }
       // drain: every peer's release of every stage has arrived here before the
@@ -783,12 +813,6 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     const int ew = e >> 5;                             // epilogue warp 0..EPI_WARPS-1
     const int quarter = warp & 3;                      // TMEM lanes 32*quarter .. +32
     const int slot = ew >> 2;                          // which of the quarter's three warps
-    // thread 0 streams each item's old texels and codes into shared memory as
-    // soon as the previous item's tiles have been written back
-    if (e == 0 && blockIdx.x < tp.items) {
-      const BlendVol& bv = a.v[vol_of(a, blockIdx.x)];
-      prefetch_item(bv.k, np, ((int)blockIdx.x - bv.item0) * np, sb, st_c, st_v, ls_c, ls_v, efull);
-    }
     // per-texel tables, built while the first stages load (the weight sums,
     // which differ per volume, when an item of a new volume starts)
     for (int t = e; t < k.Tc + k.Tv; t += EPI_THREADS) {
@@ -804,6 +828,13 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         g[ring_slot(tr[q], tc[q], n)] = (uint32_t)(tr[q] * (n + 2) + tc[q]) | ((uint32_t)src << 16);
     }
     if (e < 4) flag_mask[e] = 0;
+    pv_grid_wait();
+    // thread 0 streams each item's old texels and codes into shared memory as
+    // soon as the previous item's tiles have been written back
+    if (e == 0 && blockIdx.x < tp.items && tp.alias_stages == 0) {
+      const BlendVol& bv = a.v[vol_of(a, blockIdx.x)];
+      prefetch_item(bv.k, np, ((int)blockIdx.x - bv.item0) * np, sb, st_c, st_v, ls_c, ls_v, efull);
+    }
     constexpr bool kSplitD2 = FORM != kF32;         // d^2 as hi + lo columns
     const int kind = k.color_code;
     const bool f16 = k.state_fmt == PV_FMT_F16;
@@ -1029,8 +1060,8 @@ cudaError_t dev_info(DevInfo* d) {
 // Tile layout, stage ring and epilogue regions for volumes shaped like k, with
 // work items of at most np_want probes (fewer when shared memory demands).
 // Fills every field of tp except items, iters and the volume-dependent ones.
-cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int smem_max, TcParams& tp,
-                        size_t* smem) {
+cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int smem_max, bool alias_ok,
+                        TcParams& tp, size_t* smem) {
   const int sb = k.state_fmt == PV_FMT_F16 ? 2 : 4;
   const int ROWB = form == kF32 ? row_bytes<kF32>() : row_bytes<kF16>();
   tp.k = k;
@@ -1081,6 +1112,40 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int
   // room for less than two stages
   const size_t n_rsum = (size_t)(k.Tc + k.Tv) * 4, n_pos = (size_t)(k.Tc + k.Tv) * 2;
   const size_t n_gb = (size_t)(tp.gb_c + tp.gb_v) * 4;
+  tp.alias_stages = 0;
+  tp.w_tx = (uint32_t)((form != kF16 ? 2 : 1) * tp.ntiles * MT * ROWB);
+  if (alias_ok && cluster == 1) {
+    // One item per CTA: the ring takes all of shared memory but the tables,
+    // and the item's old texels and codes go into its first stages once the
+    // main loop no longer needs them, so the ring is about twice as deep.
+    const size_t es = ((size_t)np_want * (3 * k.sc_stride + 2 * k.sv_stride) + 8 * (size_t)k.sv_stride) * sb;
+    const size_t el = ((size_t)np_want * (3 * k.lc_stride + 2 * k.lv_stride) + 8 * (size_t)k.lv_stride) * 2;
+    const size_t tables = align1k(n_rsum) + align1k(n_pos) + align1k(n_gb) + 1024 + 1024;
+    const size_t region = align1k(es) + align1k(el);
+    int st = tables + 2048 < (size_t)smem_max ? (int)(((size_t)smem_max - 2048 - tables) / tp.stage_bytes) : 0;
+    if (st > kMaxStages) st = kMaxStages;
+    if (st >= 2 && (size_t)st * tp.stage_bytes >= region) {
+      tp.np = np_want;
+      tp.stages = st;
+      tp.alias_stages = (int)((region + tp.stage_bytes - 1) / tp.stage_bytes);
+      tp.stage_tx = (uint32_t)(4 * np_want * ROWB) + tp.w_tx;
+      tp.off_state = 0;
+      tp.off_last = (int)align1k(es);
+      size_t off = (size_t)st * tp.stage_bytes;
+      tp.off_rsum = (int)off;
+      off += align1k(n_rsum);
+      tp.off_pos = (int)off;
+      off += align1k(n_pos);
+      tp.off_gb = (int)off;
+      off += align1k(n_gb);
+      tp.off_flags = (int)off;
+      off += 1024;
+      tp.off_bar = (int)off;
+      off += 1024;
+      *smem = off + 1024;                      // slack for aligning the dynamic base
+      return cudaSuccess;
+    }
+  }
   int np = np_want;
   int stages = 0;
   size_t epi_state = 0, epi_last = 0;
@@ -1099,7 +1164,6 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int
   if (stages > kMaxStages) stages = kMaxStages;
   tp.np = np;
   tp.stages = stages;
-  tp.w_tx = (uint32_t)((form != kF16 ? 2 : 1) * tp.ntiles * MT * ROWB);
   tp.stage_tx = (uint32_t)(4 * np * ROWB) + tp.w_tx;
   off = (size_t)stages * tp.stage_bytes;
   tp.off_state = (int)off;
@@ -1225,12 +1289,16 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   TcPlan* pl = new TcPlan();
   memset(pl, 0, sizeof(TcPlan));
   TcParams& tp = pl->args.tp;
-  e = make_layout(k, form, np, cluster, di.smem_max, tp, &pl->smem);
+  // a volume whose items all fit in one wave keeps each item's old tiles in
+  // its CTA's stage ring (a deeper ring)
+  const bool one_wave = cluster == 1 && (k.P + np - 1) / np <= resident;
+  e = make_layout(k, form, np, cluster, di.smem_max, one_wave, tp, &pl->smem);
   if (e == cudaSuccess) {
     tp.items = (k.P + tp.np - 1) / tp.np;
     const int want = (tp.items + cluster - 1) / cluster * cluster;
     pl->grid = want < resident ? want : resident;
     tp.iters = (tp.items + pl->grid - 1) / pl->grid;
+    if (tp.alias_stages > 0 && tp.iters != 1) e = cudaErrorInvalidConfiguration;   // cannot happen: np kept
     pl->form = form;
     pl->args.nvol = 1;
     BlendVol& bv = pl->args.v[0];
@@ -1282,7 +1350,7 @@ cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc
   pv_tc_batch* b = new pv_tc_batch();
   memset(b, 0, sizeof(pv_tc_batch));
   TcParams& tp = b->args.tp;
-  e = make_layout(k0, form, np, 1, di.smem_max, tp, &b->smem);
+  e = make_layout(k0, form, np, 1, di.smem_max, false, tp, &b->smem);
   if (e == cudaSuccess) {
     int items = 0;
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
