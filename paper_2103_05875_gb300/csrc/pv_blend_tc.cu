@@ -1114,10 +1114,26 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int
   const size_t n_gb = (size_t)(tp.gb_c + tp.gb_v) * 4;
   tp.alias_stages = 0;
   tp.w_tx = (uint32_t)((form != kF16 ? 2 : 1) * tp.ntiles * MT * ROWB);
-  if (alias_ok && cluster == 1) {
-    // One item per CTA: the ring takes all of shared memory but the tables,
-    // and the item's old texels and codes go into its first stages once the
-    // main loop no longer needs them, so the ring is about twice as deep.
+  int np = np_want;
+  int stages = 0;
+  size_t epi_state = 0, epi_last = 0;
+  for (; np >= 1; --np) {
+    // the epilogue's last row group of a channel reads up to 7 rows past the
+    // item, so each region ends with 8 spare rows
+    epi_state = ((size_t)np * (3 * k.sc_stride + 2 * k.sv_stride) + 8 * (size_t)k.sv_stride) * sb;
+    epi_last = ((size_t)np * (3 * k.lc_stride + 2 * k.lv_stride) + 8 * (size_t)k.lv_stride) * 2;
+    const size_t epi = align1k(epi_state) + align1k(epi_last) + align1k(n_rsum) + align1k(n_pos) +
+                       align1k(n_gb) + 1024 + 1024;
+    const size_t need = 1024 + epi;
+    stages = need < (size_t)smem_max ? (int)(((size_t)smem_max - need) / tp.stage_bytes) : 0;
+    if (stages >= 2) break;
+  }
+  if (alias_ok && cluster == 1 && stages < 3) {
+    // One item per CTA and a shallow ring (the FP32 form): the ring takes all
+    // of shared memory but the tables, and the item's old texels and codes go
+    // into its first stages once the main loop no longer needs them, so the
+    // ring is about twice as deep. (With three or more stages the separate
+    // layout is faster: its old tiles load early, not behind the last chunks.)
     const size_t es = ((size_t)np_want * (3 * k.sc_stride + 2 * k.sv_stride) + 8 * (size_t)k.sv_stride) * sb;
     const size_t el = ((size_t)np_want * (3 * k.lc_stride + 2 * k.lv_stride) + 8 * (size_t)k.lv_stride) * 2;
     const size_t tables = align1k(n_rsum) + align1k(n_pos) + align1k(n_gb) + 1024 + 1024;
@@ -1145,20 +1161,6 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int
       *smem = off + 1024;                      // slack for aligning the dynamic base
       return cudaSuccess;
     }
-  }
-  int np = np_want;
-  int stages = 0;
-  size_t epi_state = 0, epi_last = 0;
-  for (; np >= 1; --np) {
-    // the epilogue's last row group of a channel reads up to 7 rows past the
-    // item, so each region ends with 8 spare rows
-    epi_state = ((size_t)np * (3 * k.sc_stride + 2 * k.sv_stride) + 8 * (size_t)k.sv_stride) * sb;
-    epi_last = ((size_t)np * (3 * k.lc_stride + 2 * k.lv_stride) + 8 * (size_t)k.lv_stride) * 2;
-    const size_t epi = align1k(epi_state) + align1k(epi_last) + align1k(n_rsum) + align1k(n_pos) +
-                       align1k(n_gb) + 1024 + 1024;
-    const size_t need = 1024 + epi;
-    stages = need < (size_t)smem_max ? (int)(((size_t)smem_max - need) / tp.stage_bytes) : 0;
-    if (stages >= 2) break;
   }
   if (stages < 2) return cudaErrorInvalidConfiguration;
   if (stages > kMaxStages) stages = kMaxStages;
