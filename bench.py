@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-client", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=20.0)
     return ap.parse_args()
 
@@ -485,6 +486,57 @@ def _served_run(arrivals, inputs, ticks, budget, slots, serial):
     return probes, lat, waiting_seen
 
 
+def client_bytes(spec):
+    """Algorithmic HBM bytes of one client decode with every probe selected: the planes and
+    delta buffers read, the full colour (float32) and visibility (binary16) tiles written."""
+    import pv_workload as wl
+    P, nc, nv = spec.probes, spec.color_interior, spec.vis_interior
+    bw, bh = spec.nx * spec.ny, spec.nz
+    planes_c = 3 * bh * nc * bw * nc * 2
+    planes_v = 3 * bh * nv * ((4 * bw * nv + 2) // 3)
+    tiles = P * (3 * (nc + 2) ** 2 * 4 + 2 * (nv + 2) ** 2 * 2)
+    return planes_c + planes_v + 2 * P * 2 + tiles
+
+
+def time_client(spec, seed, hbm_peak, peak_src, reps=30):
+    """Client side: one GPU decode (pv_client_apply) of a noisy-workload frame in which every
+    probe is selected, timed alone with CUDA events after an L2 flush (a 256 MB write)."""
+    import torch
+    import paper_2103_05875_gb300 as pv
+    import pv_workload as wl
+    fs = wl.FrameStream(spec, seed, mode="noisy")
+    vol = pv.ProbeVolume(spec)
+    rad = wl.to_operand(fs.radiance(0), spec.operand_fmt).cuda()
+    dist = wl.to_operand(fs.dist(0), spec.operand_fmt).cuda()
+    dirs = torch.from_numpy(fs.directions(0)).cuda()
+    vol.update(rad, dist, dirs)
+    fr = vol.select_and_pack(want_host_counts=True)
+    assert fr.count_c == spec.probes and fr.count_v == spec.probes
+    client = pv.ProbeClient(spec)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        client.apply(fr)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.fill_(1)
+        a.record(stream)
+        client.apply(fr)
+        b.record(stream)
+    torch.cuda.synchronize()
+    us = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)[reps // 2]
+    client.close()
+    vol.close()
+    nbytes = client_bytes(spec)
+    achieved = nbytes / (us * 1e-6) / 1e9
+    return {"workload": "client decode of a 16x16x16-probe frame, every probe selected (colour 6x6, vis 14x14)",
+            "value": spec.probes / (us * 1e-6), "unit": "probes/s", "us_per_frame": us,
+            "l2": "flushed (256 MB write) before each timed launch",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "kernel": "client_apply",
+                         "peak_source": peak_src, "algorithmic_bytes_per_launch": nbytes}}
+
+
 def time_served(seconds, seed):
     """Served form: 64 clients arriving Poisson(4/s) with exponential sessions (mean 8 s), each
     owning a volume of the batched workload's sizes; 60 Hz ticks over `seconds` of simulated
@@ -632,6 +684,8 @@ def run_ours(args, ws, rank, local):
         line["batched"] = time_batched(max(10, args.steps // 2), args.warmup, seed)
     if rank == 0 and not args.no_served:
         line["served"] = time_served(args.served_seconds, seed)
+    if rank == 0 and ws == 1 and not args.no_client:
+        line["client"] = time_client(wl.config2(), seed, hbm_peak, peak_src)
     if rank == 0 and ws == 1 and not args.no_e2e:
         line["e2e"] = time_e2e(wl.config2(operand_fmt=forms[0]), max(10, args.steps // 2), seed)
         if forms[0] != "f16" and "f16" in forms:           # half the upload bytes per frame

@@ -376,6 +376,40 @@ pv_status pv_submit(pv_server* server, int32_t client, const void* radiance, con
 pv_status pv_server_tick(pv_server* server, void* stream, uint64_t* tick);
 pv_status pv_poll(pv_server* server, uint64_t ticket, pv_frame* out);
 
+/* ----------------------------------------------------------------- client */
+/*
+ * Client side of Sections 3.3-3.4: the permanent probe textures a client keeps
+ * and the decode of each packed update into them (the GPU half of the client's
+ * repacking step; the video decode that would produce the planes is not part
+ * of this library).
+ *  pv_client_create   textures for volumes described by `desc` (the same
+ *                     description as the server volume's), zeroed:
+ *                     colour [3][P][(n_c+2)^2] float32, the exact values of
+ *                     the transmitted codes (UF10, or UNORM10 code/1023);
+ *                     visibility [2][P][(n_v+2)^2] binary16 bits (R, G), the
+ *                     transmitted RG16F texels. Each tile holds the interior
+ *                     and its octahedral guard band.
+ *  pv_client_apply    apply one frame (asynchronous on `stream`): probe ids
+ *                     from the delta-coded index buffers (delta_c/delta_v,
+ *                     16-byte aligned device buffers of at least
+ *                     count entries), the interiors of slots 0..count-1 from
+ *                     the planes, written into the tiles of those probes,
+ *                     whose guard bands are rebuilt. Reads only color_planes,
+ *                     vis_planes, delta_*, count_*_dev of the frame (device
+ *                     pointers laid out as probe_volume_info gives for
+ *                     `desc`). Counts above P are taken as P and probe ids
+ *                     at or above P are skipped. Probes not in the frame
+ *                     keep their tiles.
+ *  pv_client_textures device pointers of the textures (owned by the client).
+ * Errors: PV_ERR_INVALID (NULL frame pointer, unaligned deltas, bad desc),
+ * PV_ERR_RANGE / PV_ERR_OOM as probe_volume_create, PV_ERR_CUDA.
+ */
+typedef struct pv_client pv_client;
+pv_status pv_client_create(const pv_desc* desc, pv_client** out);
+pv_status pv_client_destroy(pv_client* client);
+pv_status pv_client_apply(pv_client* client, const pv_frame* frame, void* stream);
+pv_status pv_client_textures(const pv_client* client, float** color, uint16_t** vis);
+
 #ifdef __cplusplus
 }
 #endif

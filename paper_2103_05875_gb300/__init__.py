@@ -106,6 +106,10 @@ def _load():
         "pv_submit": (i32, [vp, i32, vp, vp, vp, C.POINTER(u64)]),
         "pv_server_tick": (i32, [vp, vp, C.POINTER(u64)]),
         "pv_poll": (i32, [vp, u64, C.POINTER(pv_frame)]),
+        "pv_client_create": (i32, [C.POINTER(pv_desc), C.POINTER(vp)]),
+        "pv_client_destroy": (i32, [vp]),
+        "pv_client_apply": (i32, [vp, C.POINTER(pv_frame), vp]),
+        "pv_client_textures": (i32, [vp, C.POINTER(vp), C.POINTER(vp)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -503,3 +507,40 @@ class ProbeServer:
         fr = pv_frame()
         st = _check(lib.pv_poll(self.handle, int(ticket), C.byref(fr)), "pv_poll")
         return None if st == PV_PENDING_STATUS else fr
+
+
+class ProbeClient:
+    """A client's permanent probe textures on the current CUDA device (pv_client_create);
+    ``apply`` decodes one packed frame into them on the GPU."""
+
+    def __init__(self, spec=None, **kw):
+        self.desc = make_desc(spec, **kw)
+        h = C.c_void_p()
+        _check(lib.pv_client_create(C.byref(self.desc), C.byref(h)), "pv_client_create")
+        self.handle = h.value
+        self.P = self.desc.nx * self.desc.ny * self.desc.nz
+        self.tc = self.desc.color_interior + 2
+        self.tv = self.desc.vis_interior + 2
+
+    def apply(self, frame: pv_frame, stream=None):
+        _check(lib.pv_client_apply(self.handle, C.byref(frame), _stream(stream)), "pv_client_apply")
+
+    def textures(self):
+        """(colour [3, P, tc, tc] float32, visibility [2, P, tv, tv] binary16 bits as uint16),
+        views of the client's device memory."""
+        import torch
+        pc, pv_ = C.c_void_p(), C.c_void_p()
+        _check(lib.pv_client_textures(self.handle, C.byref(pc), C.byref(pv_)), "pv_client_textures")
+        return (device_view(pc.value, (3, self.P, self.tc, self.tc), torch.float32),
+                device_view(pv_.value, (2, self.P, self.tv, self.tv), torch.uint16))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.pv_client_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -229,6 +229,25 @@ void pv_wait_downloads(pv_volume* v, cudaStream_t st) {
   if (v->dl_seq > 0) cudaStreamWaitEvent(st, v->ev_out[(v->dl_seq - 1) % PV_DL_RING], 0);
 }
 
+pv_status pv_frame_geometry(const pv_desc* d, pv_geom* g) {
+  const pv_status s = validate(d);
+  if (s != PV_OK) return s;
+  const Layout L = layout_of(d);
+  g->P = L.P;
+  g->nc = L.nc;
+  g->nv = L.nv;
+  g->tc = L.tc;
+  g->tv = L.tv;
+  g->bw = L.bw;
+  g->bh = L.bh;
+  g->cheight = L.cheight;
+  g->cpitch = L.cpitch;
+  g->vheight = L.vheight;
+  g->vpitch = L.vpitch;
+  g->vwidth = L.vwidth;
+  return PV_OK;
+}
+
 extern "C" {
 
 const char* pv_status_string(pv_status s) {

@@ -134,4 +134,28 @@ __device__ __forceinline__ int border_targets(int i, int j, int n, int* tr, int*
   return k;
 }
 
+// x / d for 0 <= x < 2^16 and 1 <= d <= 2^15, with m = ceil(2^31 / d)
+// (pv_rcp31): one multiply-high instead of an integer division.
+__device__ __forceinline__ int fdiv(int x, uint32_t m) { return (int)__umulhi((uint32_t)x << 1, m); }
+
+// Tile position (r, c) of an (n+2)^2 tile, 0 <= r, c <= n+1: the interior
+// texel it holds, in tile coordinates (itself for interior positions; for the
+// guard band the texel the reflection rule of Section 3.4 copies from).
+__host__ __device__ __forceinline__ void border_source(int r, int c, int n, int* sr, int* sc) {
+  const bool top = r == 0, bottom = r == n + 1, left = c == 0, right = c == n + 1;
+  if ((top || bottom) && (left || right)) {          // corners: double reflection
+    *sr = top ? n : 1;
+    *sc = left ? n : 1;
+  } else if (top || bottom) {
+    *sr = top ? 1 : n;
+    *sc = n + 1 - c;
+  } else if (left || right) {
+    *sr = n + 1 - r;
+    *sc = left ? 1 : n;
+  } else {
+    *sr = r;
+    *sc = c;
+  }
+}
+
 }  // namespace pv

@@ -82,6 +82,15 @@ struct pv_volume {
   void* tc_plan;                        // tensor-core kernel plan (tensor maps), or NULL
 };
 
+// Frame geometry of a volume description (the same for the server volume and
+// for a client that decodes its frames): PV_OK, or the validation error.
+struct pv_geom {
+  int P, nc, nv, tc, tv, bw, bh;
+  int cheight, cpitch;                  // colour plane rows, row bytes
+  int vheight, vpitch, vwidth;          // visibility plane rows, row bytes, stream bytes per row
+};
+pv_status pv_frame_geometry(const pv_desc* d, pv_geom* g);
+
 // ceil(2^31 / d); x / d == umulhi(2x, ceil(2^31 / d)) for 0 <= x < 2^16 and
 // 1 <= d <= 2^15 (the rounding excess x * (m - 2^31 / d) / 2^31 stays below 1/d).
 inline uint32_t pv_rcp31(uint32_t d) { return (uint32_t)(((1ull << 31) + d - 1) / d); }

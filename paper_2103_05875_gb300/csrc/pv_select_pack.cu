@@ -50,8 +50,7 @@ struct SpShared {
   uint32_t seq;
 };
 
-// x / d for 0 <= x < 2^16, with m = ceil(2^31 / d) (pv_rcp31)
-__device__ __forceinline__ int fdiv(int x, uint32_t m) { return (int)__umulhi((uint32_t)x << 1, m); }
+using pv::fdiv;
 
 // ceil(2^31 / d) for run lengths d = 1..SP_RANGE
 __constant__ uint32_t c_rcp_run[SP_RANGE + 1] = {0u,          0x80000000u, 0x40000000u, 0x2AAAAAABu, 0x20000000u,

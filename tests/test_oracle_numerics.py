@@ -118,3 +118,17 @@ def test_round_state_is_idempotent(fmt):
     x = np.random.default_rng(5).lognormal(0, 2, 1000)
     r = nu.round_state(x, fmt)
     np.testing.assert_array_equal(nu.round_state(r, fmt), r)
+
+
+def test_unorm10_binary32_values_are_single_rounded():
+    """The GPU client stores UNORM10 values as the correctly rounded binary32 quotient
+    code / 1023; the oracle's binary64 value rounded to binary32 must be that same number
+    (no double-rounding case among the 1024 codes)."""
+    from fractions import Fraction
+    for code in range(1024):
+        via64 = float(np.float32(code / 1023.0))
+        exact = Fraction(code, 1023)
+        f = np.float32(float(exact))
+        lo, hi = np.nextafter(f, np.float32(-1)), np.nextafter(f, np.float32(2))
+        best = min((lo, f, hi), key=lambda x: (abs(Fraction(float(x)) - exact), int(np.float32(x).view(np.uint32)) & 1))
+        assert via64 == float(best), code
