@@ -31,11 +31,14 @@ namespace {
 constexpr int CA_THREADS = 256;
 constexpr int CA_SLOTS = 8;                             // slots per block
 constexpr int CA_MAX_T = PV_MAX_INTERIOR * PV_MAX_INTERIOR;
+constexpr int CA_MAX_TILE = (PV_MAX_INTERIOR + 2) * (PV_MAX_INTERIOR + 2);
 
 struct CaArgs {
   int P, nc, nv, tc, tv, bw, cheight, cpitch, vheight, vpitch;
   int kind, lsb;
-  uint32_t rcp_nc, rcp_nv, rcp_tc, rcp_tv, rcp_tc2, rcp_tv2;
+  uint32_t rcp_nc, rcp_nv;
+  int vw_c, vw_v;                        // texels per vector store of a colour / visibility tile
+  uint32_t rcp_cvec, rcp_vvec;           // ceil(2^31 / vectors per tile)
   const uint16_t* planes_c;
   const uint8_t* planes_v;
   const uint16_t* delta_c;
@@ -50,12 +53,13 @@ struct CaShared {
   float vc[CA_SLOTS][3 * CA_MAX_T];      // decoded colour interiors of the block's slots
   uint32_t vv[CA_SLOTS][CA_MAX_T];       // visibility interiors: R | G << 16
   int id_c[CA_SLOTS], id_v[CA_SLOTS];    // probe of each slot, -1 for none
-  int bx[CA_SLOTS], by[CA_SLOTS];        // block of each slot in the update texture
+  uint16_t src_c[CA_MAX_TILE];           // per tile position: the interior texel it holds
+  uint16_t src_v[CA_MAX_TILE];
   uint32_t red[2 * CA_THREADS / 32];
-  uint32_t base_c, base_v;
 };
 
-// Sum of delta[0..n) (n a multiple of 8, 16-byte aligned buffer), block-wide.
+// Per-warp partial sums of da[0..na) and db[0..nb) (multiples of 8, 16-byte
+// aligned buffers) into sh.red, then a barrier.
 __device__ __forceinline__ void sum_two(const uint16_t* da, int na, const uint16_t* db, int nb, CaShared& sh) {
   uint32_t sa = 0, sb = 0;
   for (int q = threadIdx.x; q < na / 8; q += CA_THREADS) {
@@ -79,14 +83,27 @@ __device__ __forceinline__ void sum_two(const uint16_t* da, int na, const uint16
     sh.red[2 * wid + 1] = sb;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t a = 0, b = 0;
-    for (int w = 0; w < CA_THREADS / 32; ++w) {
-      a += sh.red[2 * w];
-      b += sh.red[2 * w + 1];
-    }
-    sh.base_c = a;
-    sh.base_v = b;
+}
+
+// Whole tiles of the block's slots, VW texels per store: vector v of channel
+// c of slot s holds tile texels VW*v .. VW*v+VW-1, each the interior texel
+// src[e] of the slot's staged values (`get`).
+template <int VW, typename V, typename T, typename G>
+__device__ __forceinline__ void store_tiles(T* tex, int P, int tt, int nch, int ns, const int* ids,
+                                            const uint16_t* src, uint32_t rcp_nvec, G get) {
+  const int nvec = tt / VW;
+  for (int it = threadIdx.x; it < ns * nch * nvec; it += CA_THREADS) {
+    const int t = pv::fdiv(it, rcp_nvec), v = it - t * nvec;
+    const int s = t / nch, c = t - s * nch;
+    const int p = ids[s];
+    if (p < 0) continue;
+    union {
+      V vec;
+      T el[VW];
+    } u;
+#pragma unroll
+    for (int q = 0; q < VW; ++q) u.el[q] = get(s, c, src[VW * v + q]);
+    *reinterpret_cast<V*>(tex + ((size_t)c * P + p) * tt + VW * v) = u.vec;
   }
 }
 
@@ -102,30 +119,20 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   const int cnt_c = (int)min(*a.count_c, (uint32_t)a.P), cnt_v = (int)min(*a.count_v, (uint32_t)a.P);
   const int ns_c = max(0, min(CA_SLOTS, cnt_c - k0)), ns_v = max(0, min(CA_SLOTS, cnt_v - k0));
   if (ns_c == 0 && ns_v == 0) return;                   // uniform: the block has no slot
-  // probe ids of the block's slots: the deltas before them, then a running sum
-  sum_two(a.delta_c, ns_c ? k0 : 0, a.delta_v, ns_v ? k0 : 0, sh);
-  if (tid == 0) {
-    uint32_t ic = sh.base_c, iv = sh.base_v;
-    for (int s = 0; s < CA_SLOTS; ++s) {
-      int pc = -1, pv = -1;
-      if (s < ns_c) {
-        ic += a.delta_c[k0 + s];
-        const int id = (int)(ic & 0xFFFFu);
-        pc = id < a.P ? id : -1;
-      }
-      if (s < ns_v) {
-        iv += a.delta_v[k0 + s];
-        const int id = (int)(iv & 0xFFFFu);
-        pv = id < a.P ? id : -1;
-      }
-      sh.id_c[s] = pc;
-      sh.id_v[s] = pv;
-      sh.by[s] = (k0 + s) / a.bw;
-      sh.bx[s] = (k0 + s) - sh.by[s] * a.bw;
-    }
-  }
-  __syncthreads();
+  // block of the update texture of the block's first slot; slot s follows
+  const int by0 = k0 / a.bw, bx0 = k0 - by0 * a.bw;
 
+  // Everything below up to the barrier is independent: the guard-band tables,
+  // the slots' interiors from the planes, and the delta sums for the ids.
+  // the guard-band rule as tables: tile position -> interior texel
+  for (int e = tid; e < a.tc * a.tc + a.tv * a.tv; e += CA_THREADS) {
+    const bool vis = e >= a.tc * a.tc;
+    const int t = vis ? a.tv : a.tc, n = vis ? a.nv : a.nc, q = vis ? e - a.tc * a.tc : e;
+    const int r = q / t, cc = q - r * t;
+    int sr, sc;
+    pv::border_source(r, cc, n, &sr, &sc);
+    (vis ? sh.src_v : sh.src_c)[q] = (uint16_t)((sr - 1) * n + (sc - 1));
+  }
   // colour interiors: items (c, i, slot, j), j fastest, so that a warp reads
   // runs of consecutive samples across neighbouring slots
   {
@@ -136,61 +143,105 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
       const int t = pv::fdiv(it, a.rcp_nc), j = it - t * n;
       const int u = pv::fdiv(t, rcp_ns), s = t - u * ns_c;
       const int c = pv::fdiv(u, a.rcp_nc), i = u - c * n;
-      const uint32_t sample =
-          a.planes_c[(size_t)c * plane + (size_t)(sh.by[s] * n + i) * (a.cpitch / 2) + sh.bx[s] * n + j];
+      int bx = bx0 + s, by = by0;
+      while (bx >= a.bw) {
+        bx -= a.bw;
+        ++by;
+      }
+      const uint32_t sample = a.planes_c[(size_t)c * plane + (size_t)(by * n + i) * (a.cpitch / 2) + bx * n + j];
       const uint32_t code = a.lsb ? (sample & 0x3FFu) : (sample >> 6);
       sh.vc[s][c * T + i * n + j] = color_value(code, a.kind);
     }
   }
-  // visibility interiors: texel (slot, i, j) takes stream bytes 4X..4X+3 of
-  // its atlas row, X = bx * n + j, byte b from plane b mod 3, column b div 3
+  // visibility interiors: an atlas row's stream bytes 12w..12w+11 (three
+  // texels) are the words at column 4w of the three planes; a thread takes one
+  // such chunk of one row of one run of slots within a block row, and keeps
+  // the texels that belong to the block's slots
   {
-    const int n = a.nv, T = n * n;
+    const int n = a.nv;
     const size_t plane = (size_t)a.vheight * a.vpitch;
-    for (int it = tid; it < ns_v * T; it += CA_THREADS) {
-      const int s = it / T, e = it - s * T;
-      const int i = pv::fdiv(e, a.rcp_nv), j = e - i * n;
-      const uint8_t* row = a.planes_v + (size_t)(sh.by[s] * n + i) * a.vpitch;
-      const int b0 = 4 * (sh.bx[s] * n + j);
-      uint32_t v = 0;
+    int by = by0, bxs = bx0;                            // block of slot s0
+    for (int s0 = 0; s0 < ns_v;) {
+      const int s1 = min(ns_v, s0 + (a.bw - bxs));      // the run s0..s1-1 shares a block row
+      const int x_lo = n * bxs, x_hi = n * (bxs + (s1 - s0));   // atlas columns of the run
+      const int w_lo = (4 * x_lo) / 12, w_hi = (4 * x_hi - 1) / 12;
+      const int nw = w_hi - w_lo + 1;
+      const uint32_t rcp_nw = (0x80000000u + (uint32_t)nw - 1u) / (uint32_t)nw;
+      for (int q = tid; q < n * nw; q += CA_THREADS) {
+        const int i = pv::fdiv(q, rcp_nw), w = w_lo + (q - i * nw);
+        const uint8_t* row = a.planes_v + (size_t)(by * n + i) * a.vpitch + 4 * (size_t)w;
+        const uint32_t p0 = *reinterpret_cast<const uint32_t*>(row);
+        const uint32_t p1 = *reinterpret_cast<const uint32_t*>(row + plane);
+        const uint32_t p2 = *reinterpret_cast<const uint32_t*>(row + 2 * plane);
+        // stream byte 12w + b sits in plane b % 3, byte b / 3 of that word
+        const uint32_t t3[3] = {__byte_perm(__byte_perm(p0, p1, 0x1040), p2, 0x3410),
+                                __byte_perm(__byte_perm(p1, p2, 0x2051), p0, 0x3610),
+                                __byte_perm(__byte_perm(p2, p0, 0x3072), p1, 0x3710)};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int b = b0 + q;
-        v |= (uint32_t)row[(size_t)(b % 3) * plane + b / 3] << (8 * q);
+        for (int e = 0; e < 3; ++e) {
+          const int X = 3 * w + e;
+          if (X >= x_lo && X < x_hi) {
+            const int so = pv::fdiv(X - x_lo, a.rcp_nv), j = X - x_lo - so * n;
+            sh.vv[s0 + so][i * n + j] = t3[e];
+          }
+        }
       }
-      sh.vv[s][e] = v;
+      s0 = s1;
+      bxs = 0;
+      ++by;
+    }
+  }
+  // probe ids: the deltas before the block's slots (block sum), and its own
+  // slots' deltas (first warp: lanes 0..7 colour, lanes 8..15 visibility)
+  uint32_t d = 0;
+  if (tid < 16) {
+    const int s = tid & 7;
+    const bool vis = tid >= 8;
+    if (s < (vis ? ns_v : ns_c)) d = vis ? a.delta_v[k0 + s] : a.delta_c[k0 + s];
+  }
+  sum_two(a.delta_c, ns_c ? k0 : 0, a.delta_v, ns_v ? k0 : 0, sh);   // ends in a barrier
+  if (tid < 32) {
+    const int lane = tid, s = lane & 7;
+    const bool vis = lane >= 8;
+    const int ns = vis ? ns_v : ns_c;
+    uint32_t base_c = 0, base_v = 0;
+    for (int w = 0; w < CA_THREADS / 32; ++w) {
+      base_c += sh.red[2 * w];
+      base_v += sh.red[2 * w + 1];
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {                   // inclusive prefix within each group of eight
+      const uint32_t t = __shfl_up_sync(0xffffffffu, d, o);
+      if (s >= o) d += t;
+    }
+    if (lane < 16) {
+      const int id = (int)(((vis ? base_v : base_c) + d) & 0xFFFFu);
+      const int p = (s < ns && id < a.P) ? id : -1;
+      if (vis) sh.id_v[s] = p;
+      else sh.id_c[s] = p;
     }
   }
   __syncthreads();
 
-  // whole tiles: interior and guard band, consecutive threads on consecutive
-  // texels of a tile
+  // whole tiles: interior and guard band, vector stores along each tile
   {
-    const int n = a.nc, tc = a.tc, tt = tc * tc, T = n * n;
-    for (int it = tid; it < ns_c * 3 * tt; it += CA_THREADS) {
-      const int t = pv::fdiv(it, a.rcp_tc2), e = it - t * tt;
-      const int s = t / 3, c = t - 3 * s;
-      const int p = sh.id_c[s];
-      if (p < 0) continue;
-      const int r = pv::fdiv(e, a.rcp_tc), cc = e - r * tc;
-      int sr, sc;
-      pv::border_source(r, cc, n, &sr, &sc);
-      a.tex_c[((size_t)c * a.P + p) * tt + e] = sh.vc[s][c * T + (sr - 1) * n + (sc - 1)];
-    }
+    const int T = a.nc * a.nc;
+    const auto get = [&](int s, int c, int e) { return sh.vc[s][c * T + e]; };
+    const int tt = a.tc * a.tc;
+    if (a.vw_c == 4) store_tiles<4, float4>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, sh.src_c, a.rcp_cvec, get);
+    else if (a.vw_c == 2) store_tiles<2, float2>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, sh.src_c, a.rcp_cvec, get);
+    else store_tiles<1, float>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, sh.src_c, a.rcp_cvec, get);
   }
   {
-    const int n = a.nv, tv = a.tv, tt = tv * tv;
-    for (int it = tid; it < ns_v * 2 * tt; it += CA_THREADS) {
-      const int t = pv::fdiv(it, a.rcp_tv2), e = it - t * tt;
-      const int s = t >> 1, c = t & 1;
-      const int p = sh.id_v[s];
-      if (p < 0) continue;
-      const int r = pv::fdiv(e, a.rcp_tv), cc = e - r * tv;
-      int sr, sc;
-      pv::border_source(r, cc, n, &sr, &sc);
-      const uint32_t v = sh.vv[s][(sr - 1) * n + (sc - 1)];
-      a.tex_v[((size_t)c * a.P + p) * tt + e] = (uint16_t)(c ? v >> 16 : v & 0xFFFFu);
-    }
+    const auto get = [&](int s, int c, int e) {
+      const uint32_t v = sh.vv[s][e];
+      return (uint16_t)(c ? v >> 16 : v & 0xFFFFu);
+    };
+    const int tt = a.tv * a.tv;
+    if (a.vw_v == 8) store_tiles<8, uint4>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, sh.src_v, a.rcp_vvec, get);
+    else if (a.vw_v == 4) store_tiles<4, uint2>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, sh.src_v, a.rcp_vvec, get);
+    else if (a.vw_v == 2) store_tiles<2, uint32_t>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, sh.src_v, a.rcp_vvec, get);
+    else store_tiles<1, uint16_t>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, sh.src_v, a.rcp_vvec, get);
   }
 }
 
@@ -271,10 +322,12 @@ pv_status pv_client_apply(pv_client* c, const pv_frame* f, void* stream) {
   a.lsb = c->d.color_lsb ? 1 : 0;
   a.rcp_nc = pv_rcp31((uint32_t)g.nc);
   a.rcp_nv = pv_rcp31((uint32_t)g.nv);
-  a.rcp_tc = pv_rcp31((uint32_t)g.tc);
-  a.rcp_tv = pv_rcp31((uint32_t)g.tv);
-  a.rcp_tc2 = pv_rcp31((uint32_t)(g.tc * g.tc));
-  a.rcp_tv2 = pv_rcp31((uint32_t)(g.tv * g.tv));
+  // widest vector store that divides a tile (the textures are 16-byte aligned)
+  const int ttc = g.tc * g.tc, ttv = g.tv * g.tv;
+  a.vw_c = ttc % 4 == 0 ? 4 : (ttc % 2 == 0 ? 2 : 1);
+  a.vw_v = ttv % 8 == 0 ? 8 : (ttv % 4 == 0 ? 4 : (ttv % 2 == 0 ? 2 : 1));
+  a.rcp_cvec = pv_rcp31((uint32_t)(ttc / a.vw_c));
+  a.rcp_vvec = pv_rcp31((uint32_t)(ttv / a.vw_v));
   a.planes_c = f->color_planes;
   a.planes_v = f->vis_planes;
   a.delta_c = f->delta_c;
