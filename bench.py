@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-client", action="store_true")
+    ap.add_argument("--no-views", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=20.0)
     return ap.parse_args()
 
@@ -537,6 +538,57 @@ def time_client(spec, seed, hbm_peak, peak_src, reps=30):
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": nbytes}}
 
 
+def time_views(seed, clients=4, frames=30, nbuf=8):
+    """Shared-volume multi-client form: one update of the 16^3 volume per frame, then one
+    selection and packing per client view (each against its own last-transmitted codes),
+    against the same clients each owning a volume that is updated and packed separately.
+    Value: client-probe updates per second (clients x probes x frames / time)."""
+    import torch
+    import paper_2103_05875_gb300 as pv
+    import pv_workload as wl
+    spec = wl.config2()
+    _, bufs = make_inputs(spec, seed, nbuf)
+    stream = torch.cuda.current_stream()
+
+    def timed(step):
+        for f in range(3):
+            step(f)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for f in range(frames):
+            step(f)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / frames
+
+    vol = pv.ProbeVolume(spec)
+    views = [pv.ProbeView(vol) for _ in range(clients)]
+
+    def shared(f):
+        vol.update(*bufs[f % nbuf])
+        for v in views:
+            v.select_and_pack()
+    ms = timed(shared)
+    for v in views:
+        v.close()
+    vol.close()
+    vols = [pv.ProbeVolume(spec) for _ in range(clients)]
+
+    def separate(f):
+        for v in vols:
+            v.update(*bufs[f % nbuf])
+            v.select_and_pack()
+    ms_sep = timed(separate)
+    for v in vols:
+        v.close()
+    P = spec.probes
+    return {"workload": f"{clients} clients of one 16x16x16-probe volume, 256 rays, noisy frames",
+            "clients": clients, "value": clients * P / (ms / 1e3), "unit": "client-probes/s",
+            "ms_per_frame": ms, "launch": "eager, CUDA events around the frames",
+            "separate_volumes": {"value": clients * P / (ms_sep / 1e3), "ms_per_frame": ms_sep}}
+
+
 def time_served(seconds, seed):
     """Served form: 64 clients arriving Poisson(4/s) with exponential sessions (mean 8 s), each
     owning a volume of the batched workload's sizes; 60 Hz ticks over `seconds` of simulated
@@ -684,6 +736,8 @@ def run_ours(args, ws, rank, local):
         line["batched"] = time_batched(max(10, args.steps // 2), args.warmup, seed)
     if rank == 0 and not args.no_served:
         line["served"] = time_served(args.served_seconds, seed)
+    if rank == 0 and ws == 1 and not args.no_views:
+        line["views"] = time_views(seed)
     if rank == 0 and ws == 1 and not args.no_client:
         line["client"] = time_client(wl.config2(), seed, hbm_peak, peak_src)
     if rank == 0 and ws == 1 and not args.no_e2e:

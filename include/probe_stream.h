@@ -410,6 +410,34 @@ pv_status pv_client_destroy(pv_client* client);
 pv_status pv_client_apply(pv_client* client, const pv_frame* frame, void* stream);
 pv_status pv_client_textures(const pv_client* client, float** color, uint16_t** vis);
 
+/* ------------------------------------------------------------------ views */
+/*
+ * Shared-volume multi-client selection (Section 3.4: one last-transmitted
+ * texture pair per client): one probe_update of a volume serves any number of
+ * views, each a client's own selection and packing against what that client
+ * has received.
+ *  pv_view_create            a view of `vol`: its own last-transmitted codes
+ *                            (nothing sent yet: its first select sends every
+ *                            probe), change masks, select state and frame
+ *                            buffers (about the volume's frame bytes plus its
+ *                            last-code bytes). The view borrows the volume:
+ *                            destroy views before their volume.
+ *  pv_view_select_and_pack   as probe_select_and_pack, against the view's own
+ *                            last codes: compares the volume's current codes
+ *                            (those of its last update) with them, then
+ *                            selects, packs into the view's frame buffers and
+ *                            records what it sent. A second select without a
+ *                            new update of the volume selects nothing. The
+ *                            volume's own probe_select_and_pack is a separate
+ *                            client and is not affected. out: host pv_frame
+ *                            whose device pointers belong to the view.
+ * Errors: PV_ERR_INVALID (NULL arguments), PV_ERR_OOM, PV_ERR_CUDA.
+ */
+typedef struct pv_view pv_view;
+pv_status pv_view_create(pv_volume* vol, pv_view** out);
+pv_status pv_view_destroy(pv_view* view);
+pv_status pv_view_select_and_pack(pv_view* view, pv_frame* out, int32_t want_host_counts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

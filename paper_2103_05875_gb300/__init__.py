@@ -110,6 +110,9 @@ def _load():
         "pv_client_destroy": (i32, [vp]),
         "pv_client_apply": (i32, [vp, C.POINTER(pv_frame), vp]),
         "pv_client_textures": (i32, [vp, C.POINTER(vp), C.POINTER(vp)]),
+        "pv_view_create": (i32, [vp, C.POINTER(vp)]),
+        "pv_view_destroy": (i32, [vp]),
+        "pv_view_select_and_pack": (i32, [vp, C.POINTER(pv_frame), i32, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -537,6 +540,41 @@ class ProbeClient:
     def close(self):
         if getattr(self, "handle", None):
             lib.pv_client_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ProbeView:
+    """One client's view of a shared ProbeVolume (pv_view_create): its own last-transmitted
+    codes, selection and packed frames. The frame accessors are the volume's."""
+
+    def __init__(self, vol: "ProbeVolume"):
+        h = C.c_void_p()
+        _check(lib.pv_view_create(vol.handle, C.byref(h)), "pv_view_create")
+        self.handle = h.value
+        self.vol = vol
+        self.desc, self.info, self.P = vol.desc, vol.info, vol.P
+        self.nc, self.nv = vol.nc, vol.nv
+
+    def select_and_pack(self, want_host_counts: bool = False, stream=None) -> pv_frame:
+        fr = pv_frame()
+        _check(lib.pv_view_select_and_pack(self.handle, C.byref(fr), int(want_host_counts), _stream(stream)),
+               "pv_view_select_and_pack")
+        return fr
+
+    color_planes = ProbeVolume.color_planes
+    vis_planes = ProbeVolume.vis_planes
+    index = ProbeVolume.index
+    counts = ProbeVolume.counts
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.pv_view_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
