@@ -55,6 +55,39 @@ def changed(codes: np.ndarray, last: np.ndarray, sent: np.ndarray) -> np.ndarray
     return differs | ~np.asarray(sent, dtype=bool)
 
 
+def changed_beyond(codes: np.ndarray, last: np.ndarray, sent: np.ndarray, threshold: int) -> np.ndarray:
+    """Section 3.4's change test with a threshold: [C, P, T] codes vs last-transmitted codes ->
+    [P] bool, true when some texel's code moved by more than ``threshold`` code steps (or the
+    probe was never sent). Reading: colour codes are 10-bit unsigned integers, visibility codes
+    binary16 bit patterns of non-negative values, so a step is one code value / one ulp;
+    threshold 0 is the texel-for-texel rule."""
+    dist = np.abs(codes.astype(np.int64) - last.astype(np.int64))
+    return np.any(dist > threshold, axis=(0, 2)) | ~np.asarray(sent, dtype=bool)
+
+
+def budget_select(flags: np.ndarray, active, cursor: int, budget: int):
+    """Per-client probe budget (Section 3.4, the per-client 'knob'): of the changed, active
+    probes, the first ``budget`` in cyclic probe order from ``cursor`` (0: no limit). Returns the
+    kept flags and the next cursor (one past the last kept probe; unchanged if none kept).
+    Reading: the cursor walks round-robin so that probes left out are sent on later frames."""
+    f = np.asarray(flags, dtype=bool).copy()
+    if active is not None:
+        f &= np.asarray(active, dtype=bool)
+    P = f.size
+    if budget <= 0 or int(f.sum()) <= budget:
+        kept = f
+    else:
+        order = np.r_[cursor:P, 0:cursor]
+        take = order[f[order]][:budget]
+        kept = np.zeros(P, dtype=bool)
+        kept[take] = True
+    if budget > 0 and kept.any():
+        order = np.r_[cursor:P, 0:cursor]
+        last = order[kept[order]][-1]
+        cursor = (int(last) + 1) % P
+    return kept, cursor
+
+
 def select(flags: np.ndarray):
     """Probe index buffer: (ids ascending uint16, delta-encoded uint16, count)."""
     idx = np.nonzero(np.asarray(flags, dtype=bool))[0]

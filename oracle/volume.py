@@ -85,11 +85,20 @@ class OracleVolume:
         return (select_pack.color_codes(self.tiles_c, self.spec.color_code),
                 select_pack.vis_codes(self.tiles_v))
 
-    def select_and_pack(self) -> Frame:
-        """Compare with last-transmitted codes, select, pack, and record what is sent."""
+    def select_and_pack(self, threshold_c: int = 0, threshold_v: int = 0, active=None, budget: int = 0) -> Frame:
+        """Compare with last-transmitted codes, select, pack, and record what is sent.
+
+        Defaults are Section 3.4's rule (every probe not texel-for-texel identical). The
+        options are the per-client selection knobs of the same section: a change threshold in
+        code steps, an active-probe mask and a per-frame probe budget taken round-robin
+        (separate cursors for the colour and visibility textures).
+        """
         codes_c, codes_v = self.codes()
-        fc = select_pack.changed(codes_c, self.last_c, self.sent_c)
-        fv = select_pack.changed(codes_v, self.last_v, self.sent_v)
+        fc = select_pack.changed_beyond(codes_c, self.last_c, self.sent_c, threshold_c)
+        fv = select_pack.changed_beyond(codes_v, self.last_v, self.sent_v, threshold_v)
+        if active is not None or budget > 0:
+            fc, self.cursor_c = select_pack.budget_select(fc, active, getattr(self, "cursor_c", 0), budget)
+            fv, self.cursor_v = select_pack.budget_select(fv, active, getattr(self, "cursor_v", 0), budget)
         idx_c, dc, nc = select_pack.select(fc)
         idx_v, dv, nv = select_pack.select(fv)
         planes_c = select_pack.pack_color(codes_c, idx_c, self.bw, self.bh, self.spec.color_lsb)

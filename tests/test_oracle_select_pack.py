@@ -187,3 +187,76 @@ def test_client_round_trip_recovers_server_textures():
         client_v = sp.client_apply(client_v, idx_v, numerics.fp16_value(cv))
         np.testing.assert_array_equal(client_v, ov.tiles_v)                 # lossless RG16F
         np.testing.assert_array_equal(numerics.uf10_code(client_c), numerics.uf10_code(ov.tiles_c))
+
+
+# ----------------------------------------------------------------- per-client selection knobs
+def test_threshold_zero_is_the_texel_for_texel_rule():
+    rng = np.random.default_rng(5)
+    codes = rng.integers(0, 1024, (3, 40, 9)).astype(np.uint16)
+    last = codes.copy()
+    last[:, ::3] ^= 1                                    # one code step apart
+    sent = rng.random(40) < 0.8
+    np.testing.assert_array_equal(sp.changed_beyond(codes, last, sent, 0), sp.changed(codes, last, sent))
+
+
+def test_threshold_brute_force():
+    rng = np.random.default_rng(6)
+    codes = rng.integers(0, 1024, (2, 25, 4)).astype(np.uint16)
+    last = (codes.astype(np.int64) + rng.integers(-3, 4, codes.shape)).clip(0, 1023).astype(np.uint16)
+    sent = np.ones(25, dtype=bool)
+    sent[7] = False
+    for th in range(5):
+        want = [not sent[p] or any(abs(int(codes[c, p, t]) - int(last[c, p, t])) > th
+                                   for c in range(2) for t in range(4)) for p in range(25)]
+        np.testing.assert_array_equal(sp.changed_beyond(codes, last, sent, th), want)
+    # a never-sent probe (sentinel codes) is changed at any threshold
+    assert sp.changed_beyond(codes, np.full_like(codes, sp.SENTINEL), np.zeros(25, bool), 1000).all()
+
+
+def test_budget_round_robin_sends_each_changed_probe_once_per_cycle():
+    P, B = 23, 5
+    flags = np.zeros(P, dtype=bool)
+    flags[[0, 2, 3, 7, 8, 9, 11, 15, 16, 20, 22]] = True
+    cursor, frames = 0, []
+    for _ in range(3):                                   # 11 changed probes, 5 per frame
+        kept, cursor = sp.budget_select(flags, None, cursor, B)
+        assert kept.sum() <= B and not (kept & ~flags).any()
+        frames.append(list(np.nonzero(kept)[0]))
+    assert frames[0] == [0, 2, 3, 7, 8] and frames[1] == [9, 11, 15, 16, 20]
+    assert frames[2] == [0, 2, 3, 7, 22]                 # 22 ends the cycle, 0, 2, 3, 7 start the next
+    assert sorted(frames[0] + frames[1] + [22]) == list(np.nonzero(flags)[0])
+    assert cursor == 8
+    # no budget, or a budget above the count, keeps every changed probe and the cursor
+    for b in (0, 11, 40):
+        kept, c = sp.budget_select(flags, None, 4, b)
+        np.testing.assert_array_equal(kept, flags)
+        assert c == 4                                    # one past the last kept probe, cyclically from 4
+
+
+def test_active_mask_excludes_inactive_probes():
+    flags = np.ones(10, dtype=bool)
+    active = np.array([1, 0, 1, 1, 0, 0, 1, 0, 1, 1], dtype=bool)
+    kept, _ = sp.budget_select(flags, active, 0, 0)
+    np.testing.assert_array_equal(kept, active)
+    kept, c = sp.budget_select(flags, active, 3, 2)
+    np.testing.assert_array_equal(np.nonzero(kept)[0], [3, 6])
+    assert c == 7
+
+
+def test_oracle_volume_budget_catches_up_over_frames():
+    """With a budget, probes left out stay changed and go out on the next frames; the
+    client's texels end equal to the full selection's after enough frames."""
+    spec = wl.VolumeSpec(3, 2, 2, 16, hysteresis=0.0, state_fmt="f16")
+    fs = wl.FrameStream(spec, 3, mode="stationary")
+    full, lim = OracleVolume(spec), OracleVolume(spec)
+    counts = []
+    for f in range(5):
+        args = tuple(np.asarray(x, dtype=np.float64) for x in (fs.radiance(f), fs.dist(f), fs.directions(f)))
+        full.update(*args)
+        lim.update(*args)
+        full.select_and_pack()
+        fr = lim.select_and_pack(budget=5)
+        counts.append(fr.count_c)
+    assert counts[:3] == [5, 5, 2] and counts[3:] == [0, 0]
+    np.testing.assert_array_equal(lim.last_c, full.last_c)
+    np.testing.assert_array_equal(lim.last_v, full.last_v)
