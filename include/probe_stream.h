@@ -434,7 +434,30 @@ pv_status pv_client_textures(const pv_client* client, float** color, uint16_t** 
  * Errors: PV_ERR_INVALID (NULL arguments), PV_ERR_OOM, PV_ERR_CUDA.
  */
 typedef struct pv_view pv_view;
+/*
+ * Per-client selection knobs (Section 3.4; all off by default):
+ *  active       device [P] bytes, nonzero for an active probe (one that may
+ *               shade the client's scene); inactive probes are never sent.
+ *               NULL: every probe active. Borrowed: must stay valid while
+ *               the view selects.
+ *  budget       at most this many probes per texture and frame (0: no
+ *               limit), the first changed active probes in cyclic probe order
+ *               from a per-texture cursor that then moves one past the last
+ *               probe sent; probes left out stay changed and go out later.
+ *  threshold_c  a probe's colour counts as changed when some texel's 10-bit
+ *               code moved by more than this many code values (0: the
+ *               texel-for-texel rule). Never-sent probes always count.
+ *  threshold_v  the same for visibility, in binary16 ulps.
+ * pv_view_set_options: PV_ERR_INVALID for negative values.
+ */
+typedef struct pv_view_opts {
+  const uint8_t* active;
+  int32_t budget;
+  int32_t threshold_c;
+  int32_t threshold_v;
+} pv_view_opts;
 pv_status pv_view_create(pv_volume* vol, pv_view** out);
+pv_status pv_view_set_options(pv_view* view, const pv_view_opts* opts);
 pv_status pv_view_destroy(pv_view* view);
 pv_status pv_view_select_and_pack(pv_view* view, pv_frame* out, int32_t want_host_counts, void* stream);
 

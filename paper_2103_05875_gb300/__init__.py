@@ -61,6 +61,11 @@ class pv_frame(C.Structure):
                 ("count_c", C.c_int64), ("count_v", C.c_int64), ("frame", C.c_uint64)]
 
 
+class pv_view_opts(C.Structure):
+    _fields_ = [("active", C.c_void_p), ("budget", C.c_int32), ("threshold_c", C.c_int32),
+                ("threshold_v", C.c_int32)]
+
+
 class pv_server_desc(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_slots", C.c_int32), ("max_batch", C.c_int32)]
 
@@ -113,6 +118,7 @@ def _load():
         "pv_view_create": (i32, [vp, C.POINTER(vp)]),
         "pv_view_destroy": (i32, [vp]),
         "pv_view_select_and_pack": (i32, [vp, C.POINTER(pv_frame), i32, vp]),
+        "pv_view_set_options": (i32, [vp, C.POINTER(pv_view_opts)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -566,6 +572,13 @@ class ProbeView:
         _check(lib.pv_view_select_and_pack(self.handle, C.byref(fr), int(want_host_counts), _stream(stream)),
                "pv_view_select_and_pack")
         return fr
+
+    def set_options(self, active=None, budget: int = 0, threshold_c: int = 0, threshold_v: int = 0):
+        """Per-client knobs: active (device uint8 [P] tensor, kept alive here), probe budget per
+        texture and frame, change thresholds in code steps (see pv_view_set_options)."""
+        self._active = active
+        o = pv_view_opts(_ptr(active), int(budget), int(threshold_c), int(threshold_v))
+        _check(lib.pv_view_set_options(self.handle, C.byref(o)), "pv_view_set_options")
 
     color_planes = ProbeVolume.color_planes
     vis_planes = ProbeVolume.vis_planes

@@ -22,11 +22,15 @@ class _OracleClient:
         self.last_c = np.full((3, spec.probes, spec.color_interior ** 2), sp.SENTINEL, dtype=np.uint16)
         self.last_v = np.full((2, spec.probes, spec.vis_interior ** 2), sp.SENTINEL, dtype=np.uint16)
 
-    def select(self, tiles_c, tiles_v, frame):
+        self.cursor_c = self.cursor_v = 0
+
+    def select(self, tiles_c, tiles_v, frame, **knobs):
         ov = OracleVolume(self.spec)
         ov.load_state(tiles_c, tiles_v, self.last_c, self.last_v, frame=frame)
-        fr = ov.select_and_pack()
+        ov.cursor_c, ov.cursor_v = self.cursor_c, self.cursor_v
+        fr = ov.select_and_pack(**knobs)
         self.last_c, self.last_v = ov.last_c.copy(), ov.last_v.copy()
+        self.cursor_c, self.cursor_v = ov.cursor_c, ov.cursor_v
         return fr
 
 
@@ -83,5 +87,37 @@ def test_view_equals_volume_selection_on_a_noisy_stream():
         torch.cuda.synchronize()
         for key in gv:
             np.testing.assert_array_equal(np.asarray(gw[key]), np.asarray(gv[key]), err_msg=key)
+    view.close()
+    vol.close()
+
+
+@pytest.mark.parametrize("budget,th_c,th_v,masked", [(0, 2, 40, False), (17, 0, 0, False), (13, 1, 8, True),
+                                                     (200, 0, 0, True)])
+def test_view_knobs_match_oracle(budget, th_c, th_v, masked):
+    """Budget (round robin, colour and visibility cursors), change thresholds and an active
+    mask on a noisy stream with h = 0.97: every frame equals the oracle's bit for bit."""
+    pv = H.lib()
+    spec = wl.VolumeSpec(7, 3, 4, 64, state_fmt="f16")
+    P = spec.probes
+    vol = pv.ProbeVolume(spec)
+    view = pv.ProbeView(vol)
+    active = None
+    if masked:
+        act = (np.arange(P) % 4 != 1)
+        active = act
+        view.set_options(torch.from_numpy(act.astype(np.uint8)).cuda(), budget, th_c, th_v)
+    else:
+        view.set_options(None, budget, th_c, th_v)
+    oc = _OracleClient(spec)
+    fs = wl.FrameStream(spec, 23, mode="noisy")
+    for f in range(6):
+        (r, d, q), _ = H.device_inputs(fs, f)
+        vol.update(r, d, q)
+        tc, tv, _, _, fno = H.gpu_state(vol)
+        fr = view.select_and_pack(want_host_counts=True)
+        ofr = oc.select(tc, tv, fno, threshold_c=th_c, threshold_v=th_v, active=active, budget=budget)
+        H.assert_frames_equal(H.gpu_frame(view, fr), ofr)
+        if budget:
+            assert fr.count_c <= budget and fr.count_v <= budget
     view.close()
     vol.close()
