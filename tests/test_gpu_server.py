@@ -130,3 +130,37 @@ def test_admission_by_memory_and_slots():
     assert e.value.status == -2
     server.close_server()
     small.close_server()
+
+
+def test_clients_update_at_their_own_rates():
+    """Variable update rates (Section 5): a client submitting every third tick is updated at a
+    third of the rate, and its results equal the same cadence served alone."""
+    ticks = 6
+    specs = {0: X, 1: OTHERS[0]}
+    inputs = _inputs(specs, ticks, seed=31)
+
+    def run(clients):
+        pv = H.lib()
+        server = pv.ProbeServer(40 << 30, 64)
+        for c in clients:
+            assert server.open(c, specs[c])
+        out = []
+        for t in range(ticks):
+            due = [c for c in clients if c == 0 or t % 3 == 0]       # client 1 every third tick
+            tickets = {c: server.submit(c, *inputs[c][t]) for c in due}
+            server.tick()
+            frames = {c: _wait(server, tk) for c, tk in tickets.items()}
+            if 1 in frames:
+                v1 = server.volume(1)
+                out.append((t, _frame_copy(v1, frames[1]), H.gpu_state(v1)))
+        server.close_server()
+        return out
+
+    mixed, alone = run([0, 1]), run([1])
+    assert [t for t, _, _ in mixed] == [0, 3] == [t for t, _, _ in alone]
+    for (_, fm, sm), (_, fa, sa) in zip(mixed, alone):
+        for key in fm:
+            np.testing.assert_array_equal(fm[key], fa[key], err_msg=key)
+        for x, y in zip(sm[:4], sa[:4]):
+            np.testing.assert_array_equal(x, y)
+        assert sm[4] == sa[4]
