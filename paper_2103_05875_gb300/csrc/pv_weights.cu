@@ -73,7 +73,12 @@ __device__ __forceinline__ void store_plane(void* base, size_t i, float w, int f
 }
 
 // Weights of texel tg (colour texels first) of volume k; one block of 256
-// threads.
+// threads, at most PV_MAX_RAYS / 256 rays per thread. All arithmetic (cosine,
+// power, operand split, the block's weight sum) runs before the wait for the
+// previous kernel; only the stores come after it, since the previous blend of
+// the volume may still read the weight images and sums.
+constexpr int kRaysPerThread = (PV_MAX_RAYS + 255) / 256;
+
 __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __restrict__ dirs, int want_rt,
                                               int want_op, int tg, bool first_block) {
   const int T = k.Tc + k.Tv;
@@ -91,14 +96,13 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
   const float sq_lo = fmaf(-sq, sq, Q) / (2.0f * sq);   // sqrt(Q) ~= sq + sq_lo
   const float s = k.sharpness;
 
-  // Operand-format copy for the tensor-core blend: shared-memory tile images
-  // (pv_w_image_offset), visibility texels in rows 0.., colour from w_vb.
-  const int op_row = vis ? t : k.w_vb + t;
-  const int eb = k.operand_fmt == PV_FMT_F32 ? 4 : 2;
-  const size_t plane = (size_t)k.w_chunks * k.w_rows * k.w_rb;   // bytes per operand plane
-
+  OpWeight o[kRaysPerThread];
   float part = 0.0f;
-  for (int r = threadIdx.x; r < k.R; r += blockDim.x) {
+#pragma unroll
+  for (int u = 0; u < kRaysPerThread; ++u) {
+    const int r = threadIdx.x + 256 * u;
+    o[u] = OpWeight{0.0f, 0.0f, 0.0f};
+    if (r >= k.R) continue;
     const float dx = dirs[3 * r + 0], dy = dirs[3 * r + 1], dz = dirs[3 * r + 2];
     float p1, e1, p2, e2, p3, e3, s12, f12, sd, f3;
     two_prod(fx, dx, p1, e1);
@@ -119,14 +123,8 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
     } else {
       w = c_hi > 0.0f ? powf(c_hi, s) * fmaf(s, c_lo / c_hi, 1.0f) : 0.0f;
     }
-    const OpWeight o = split_weight(w, k.operand_fmt, vis);
-    if (want_rt) k.w_rt[(size_t)r * T + tg] = o.eff;
-    if (want_op) {
-      uint8_t* img = reinterpret_cast<uint8_t*>(k.w_op) + pv_w_image_offset(k, op_row, r, eb);
-      store_plane(img, 0, o.hi, k.operand_fmt);
-      if (k.operand_fmt != PV_FMT_F16) store_plane(img + plane, 0, o.lo, k.operand_fmt);
-    }
-    part += o.eff;
+    o[u] = split_weight(w, k.operand_fmt, vis);
+    part += o[u].eff;
   }
   // deterministic block reduction of the weight sum
   __shared__ float red[256];
@@ -135,6 +133,24 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
+  }
+
+  pv_grid_wait();                     // stores only from here on
+  // Operand-format copy for the tensor-core blend: shared-memory tile images
+  // (pv_w_image_offset), visibility texels in rows 0.., colour from w_vb.
+  const int op_row = vis ? t : k.w_vb + t;
+  const int eb = k.operand_fmt == PV_FMT_F32 ? 4 : 2;
+  const size_t plane = (size_t)k.w_chunks * k.w_rows * k.w_rb;   // bytes per operand plane
+#pragma unroll
+  for (int u = 0; u < kRaysPerThread; ++u) {
+    const int r = threadIdx.x + 256 * u;
+    if (r >= k.R) continue;
+    if (want_rt) k.w_rt[(size_t)r * T + tg] = o[u].eff;
+    if (want_op) {
+      uint8_t* img = reinterpret_cast<uint8_t*>(k.w_op) + pv_w_image_offset(k, op_row, r, eb);
+      store_plane(img, 0, o[u].hi, k.operand_fmt);
+      if (k.operand_fmt != PV_FMT_F16) store_plane(img + plane, 0, o[u].lo, k.operand_fmt);
+    }
   }
   if (threadIdx.x == 0) k.sums[tg] = red[0];
 
@@ -151,7 +167,6 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
 __global__ void __launch_bounds__(256) k_weights(pv_dev k, const float* __restrict__ dirs,
                                                  int want_rt, int want_op) {
   pv_grid_launch_dependents();
-  pv_grid_wait();
   weights_block(k, dirs, want_rt, want_op, blockIdx.x, blockIdx.x == 0);
 }
 
@@ -164,9 +179,8 @@ struct WeightsBatch {
 __global__ void __launch_bounds__(256) k_weights_batch(const __grid_constant__ WeightsBatch b, int want_rt,
                                                        int want_op) {
   pv_grid_launch_dependents();
-  pv_grid_wait();
   const pv_dev& k = b.k[blockIdx.y];
-  if ((int)blockIdx.x >= k.Tc + k.Tv) return;
+  if ((int)blockIdx.x >= k.Tc + k.Tv) return;          // no texel: writes nothing
   weights_block(k, b.dirs[blockIdx.y], want_rt, want_op, blockIdx.x, blockIdx.x == 0);
 }
 
