@@ -67,6 +67,10 @@ CHAIN_CASES = {
                                       state_fmt="f16"), 4, "noisy"),
     "unorm10_lsb": (_spec(nx=2, ny=3, nz=4, rays=48, color_code="unorm10", color_lsb=True), 3, "noisy"),
     "stationary_first_frame": (_spec(state_fmt="f16", first_frame_no_hysteresis=True), 4, "stationary"),
+    # the largest shapes: 1024 rays (64 K chunks of 16), and 65,536 probes (the whole 2-byte
+    # index range, 2,048 mask words, many items per CTA)
+    "max_rays_1024": (_spec(nx=2, ny=2, nz=2, rays=1024, state_fmt="f16"), 2, "noisy"),
+    "max_probes_65536": (_spec(nx=256, ny=16, nz=16, rays=8, state_fmt="f16"), 1, "noisy"),
 }
 
 
