@@ -1,6 +1,8 @@
 """GPU parity tests: the CUDA path, called through the C ABI, against the FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (each derived from the arithmetic: 3xTF32 products carry <= 2^-21 relative error
+and FP32 accumulation over <= 1024 terms stays below 1e-5 on the normalised mean; the 16-bit
+operand forms carry the weights' and inputs' rounding, the precision form's 2e-3 budget):
   * blended mean m, FP32 operands:      relative error <= 1e-5 vs FP64
   * blended mean m, FP16/BF16 operands: relative error <= 2e-3 vs FP64
   * FP16 state, one frame from identical texels: <= 1 binary16 ulp per texel
@@ -116,9 +118,9 @@ def test_blend_mean_accuracy_full_size(operand_fmt, tol, kernel):
     line = (f"{operand_fmt}/{vol.kernel}: colour max {ec.max():.3e} mean {ec.mean():.3e}; "
             f"visibility max {ev.max():.3e} mean {ev.mean():.3e}")
     print("\n" + line)
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
-        with open(os.path.join(out, "accuracy.txt"), "a") as f:
+    out = os.environ.get("PV_ACCURACY_LOG")            # optional: append the figures to a file
+    if out:
+        with open(out, "a") as f:
             f.write(line + "\n")
     assert ec.max() <= tol
     assert ev.max() <= tol
