@@ -48,6 +48,7 @@ struct SpShared {
   int n_c, n_v, first_c, first_v;          // how many, and the slot of the first
   int tot_c, tot_v, prev_cnt_c, prev_cnt_v;
   uint32_t seq;
+  uint16_t xoff[SP_RANGE * PV_MAX_INTERIOR];   // per texel column of a visibility run: its staged row 0
 };
 
 using pv::fdiv;
@@ -87,8 +88,18 @@ __device__ __forceinline__ void write_color_run(const pv_dev& k, const SpShared&
 // byte-permuted from the three texels; the run's first and last chunks share
 // bytes with neighbouring slots (written by other blocks) and are written byte
 // by byte, only where they belong to these slots.
-__device__ __forceinline__ void write_vis_run(const pv_dev& k, const SpShared& sh, int a, int b, int q0, bool clear) {
+__device__ __forceinline__ void write_vis_run(const pv_dev& k, SpShared& sh, int a, int b, int q0, bool clear) {
   const int n = k.nv, by = a / k.bw, bx0 = a - by * k.bw;
+  // the run's texel columns -> offset of their row-0 R code in the staging area
+  // (block-uniform: every thread of the block takes the same runs)
+  if (!clear) {
+    for (int X = threadIdx.x; X < n * (b - a); X += SP_THREADS) {
+      const int so = fdiv(X, k.rcp_nv), j = X - so * n;
+      sh.xoff[X] = (uint16_t)(sh.list_v[q0 + so] * (2 * SP_MAX_T) + j);
+    }
+    __syncthreads();
+  }
+  const uint16_t* cv0 = &sh.cv[0][0];
   const int s_lo = 4 * n * bx0, s_hi = 4 * n * (bx0 + (b - a));   // stream bytes [s_lo, s_hi)
   const int w_lo = s_lo / 12, w_hi = (s_hi - 1) / 12;             // chunks touched
   const int nw = w_hi - w_lo + 1;
@@ -102,8 +113,7 @@ __device__ __forceinline__ void write_vis_run(const pv_dev& k, const SpShared& s
       const int X = 3 * w + e - n * bx0;                          // texel column within the run
       t3[e] = 0u;
       if (!clear && X >= 0 && X < n * (b - a)) {
-        const int so = fdiv(X, k.rcp_nv), j = X - so * n;
-        const uint16_t* src = sh.cv[sh.list_v[q0 + so]] + i * n + j;
+        const uint16_t* src = cv0 + sh.xoff[X] + i * n;
         t3[e] = (uint32_t)src[0] | (uint32_t)src[k.lv_stride] << 16;
       }
     }
@@ -126,6 +136,7 @@ __device__ __forceinline__ void write_vis_run(const pv_dev& k, const SpShared& s
         }
     }
   }
+  if (!clear) __syncthreads();                                  // the table is rebuilt by the next run
 }
 
 // Slots [s0, s1) split into runs within one block row; each run written by
