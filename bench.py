@@ -65,8 +65,10 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
+        # one process per GPU over NCCL; gloo where no GPU is visible (host-side tests)
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend=backend)
     return ws, rank, local
 
@@ -82,9 +84,15 @@ def max_over_ranks(x: float, ws: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(units_per_rank: int, steps: int, ws: int, t_max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed, over the slowest rank's time."""
+    return units_per_rank * steps * ws / (t_max_ms / 1e3)
 
 
 class Clocks:
@@ -704,7 +712,7 @@ def run_ours(args, ws, rank, local):
     head = results[forms[0]]
     t_max = max_over_ranks(head["total_ms"], ws)
     P = 4096
-    value = P * args.steps * ws / (t_max / 1e3)
+    value = job_value(P, args.steps, ws, t_max)
     op_bytes = 4 if forms[0] == "f32" else 2
     bpp = blend_bytes_per_probe(256, op_bytes)
     alg = bpp * P + (36 + 196) * 256 * 4
