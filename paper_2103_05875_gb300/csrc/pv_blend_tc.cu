@@ -25,7 +25,7 @@
 //
 // Operand forms (pv_desc.operand_fmt):
 //   F16  kind::f16, binary16 inputs; visibility weights scaled by 2^15 and
-//        d^2 by 2^-8 (both undone exactly) to stay in range.
+//        d^2 by 2^-4 (both undone exactly) to stay in range.
 //   BF16 kind::f16 with bfloat16; W = W_hi + W_lo (two MMAs) because one
 //        bfloat16 weight only carries 8 bits.
 //   F32  kind::tf32, float32 inputs; x = x_hi + x_lo and W = W_hi + W_lo with
@@ -38,15 +38,24 @@
 //   warp 1     TMEM allocation and the single MMA-issuing thread
 //   warps 2-3  converters: d^2 rows, TF32 hi/lo split
 //   warps 4-15 epilogue. A lane owns one texel (its TMEM lane) and a task is
-//              one 32-column load: 32 probe rows of one channel of that texel.
-//              Per row the fused work of Sections 3.2-3.4 runs with every
-//              per-texel constant in registers (weight-sum normalisation,
-//              hysteresis, storage rounding, transmitted code, comparison with
-//              the last-transmitted code, changed flags) on the item's tiles in
-//              shared memory; the guard band is copied afterwards for all rows,
-//              and the tiles go back to HBM by bulk copies. The item's old
-//              texels and codes are streamed in by bulk copies while the
-//              previous item is still being processed.
+//              one channel of a 32-texel group over the item's probe rows,
+//              loaded from TMEM eight columns at a time. Per row the fused
+//              work of Sections 3.2-3.4 runs with every per-texel constant in
+//              registers (weight-sum normalisation, hysteresis, storage
+//              rounding, transmitted code, comparison with the
+//              last-transmitted code, changed flags) on the item's tiles in
+//              shared memory; each new code replaces the last one in the code
+//              tile. The guard band is copied afterwards for all rows, and the
+//              tiles and the current codes (which select/pack sends) go back
+//              to HBM by bulk copies. The item's old texels and codes are
+//              streamed in by bulk copies while the previous item is still
+//              being processed; when every CTA has one item and the separate
+//              layout would leave a shallow ring, they live in the ring's
+//              first stages instead and are loaded once those stages are free.
+// Programmatic dependent launch: the kernel lets its successor launch at its
+// start and runs its set-up (barriers, TMEM, tensor-map prefetch, parameter
+// reads) before waiting for its predecessor; each role waits only before its
+// first read of memory a predecessor wrote.
 // Accumulators are double-buffered in TMEM (columns 0 and 256) when a buffer
 // needs at most 256 columns, so an item's epilogue overlaps the next item's
 // MMAs. Every mbarrier wait is
