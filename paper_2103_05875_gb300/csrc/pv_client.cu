@@ -29,9 +29,7 @@ struct pv_client {
 namespace {
 
 constexpr int CA_THREADS = 256;
-constexpr int CA_SLOTS = 8;                             // slots per block
-constexpr int CA_MAX_T = PV_MAX_INTERIOR * PV_MAX_INTERIOR;
-constexpr int CA_MAX_TILE = (PV_MAX_INTERIOR + 2) * (PV_MAX_INTERIOR + 2);
+constexpr int CA_SLOTS = 4;                             // slots per block (a power of two, <= 16)
 
 struct CaArgs {
   int P, nc, nv, tc, tv, bw, cheight, cpitch, vheight, vpitch;
@@ -49,17 +47,22 @@ struct CaArgs {
   uint16_t* tex_v;
 };
 
+// Shared memory sized to the volume's interiors (dynamic, after this struct):
+//   float    vc[CA_SLOTS][3][Tc]   decoded colour interiors of the block's slots
+//   uint32_t vv[CA_SLOTS][Tv]      visibility interiors: R | G << 16
+//   uint16_t src_c[tc*tc], src_v[tv*tv]   per tile position: the interior texel it holds
 struct CaShared {
-  float vc[CA_SLOTS][3 * CA_MAX_T];      // decoded colour interiors of the block's slots
-  uint32_t vv[CA_SLOTS][CA_MAX_T];       // visibility interiors: R | G << 16
   int id_c[CA_SLOTS], id_v[CA_SLOTS];    // probe of each slot, -1 for none
-  uint16_t src_c[CA_MAX_TILE];           // per tile position: the interior texel it holds
-  uint16_t src_v[CA_MAX_TILE];
   uint32_t red[2 * CA_THREADS / 32];
 };
 
-// Per-warp partial sums of da[0..na) and db[0..nb) (multiples of 8, 16-byte
-// aligned buffers) into sh.red, then a barrier.
+size_t ca_dyn_bytes(int nc, int nv) {
+  return (size_t)CA_SLOTS * 3 * nc * nc * 4 + (size_t)CA_SLOTS * nv * nv * 4 + (size_t)(nc + 2) * (nc + 2) * 2 +
+         (size_t)(nv + 2) * (nv + 2) * 2;
+}
+
+// Per-warp partial sums of da[0..na) and db[0..nb) (16-byte aligned buffers;
+// eight at a time, then the tail) into sh.red, then a barrier.
 __device__ __forceinline__ void sum_two(const uint16_t* da, int na, const uint16_t* db, int nb, CaShared& sh) {
   uint32_t sa = 0, sb = 0;
   for (int q = threadIdx.x; q < na / 8; q += CA_THREADS) {
@@ -72,6 +75,8 @@ __device__ __forceinline__ void sum_two(const uint16_t* da, int na, const uint16
     sb += (v.x & 0xFFFFu) + (v.x >> 16) + (v.y & 0xFFFFu) + (v.y >> 16) + (v.z & 0xFFFFu) + (v.z >> 16) +
           (v.w & 0xFFFFu) + (v.w >> 16);
   }
+  for (int q = 8 * (na / 8) + (int)threadIdx.x; q < na; q += CA_THREADS) sa += da[q];
+  for (int q = 8 * (nb / 8) + (int)threadIdx.x; q < nb; q += CA_THREADS) sb += db[q];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     sa += __shfl_xor_sync(0xffffffffu, sa, o);
@@ -114,6 +119,12 @@ __device__ __forceinline__ float color_value(uint32_t code, int kind) {
 
 __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   __shared__ __align__(16) CaShared sh;
+  extern __shared__ __align__(16) uint8_t ca_dyn[];
+  const int Tc = a.nc * a.nc, Tv = a.nv * a.nv;
+  float* vc = reinterpret_cast<float*>(ca_dyn);
+  uint32_t* vv = reinterpret_cast<uint32_t*>(vc + CA_SLOTS * 3 * Tc);
+  uint16_t* src_c = reinterpret_cast<uint16_t*>(vv + CA_SLOTS * Tv);
+  uint16_t* src_v = src_c + a.tc * a.tc;
   const int tid = threadIdx.x;
   const int k0 = blockIdx.x * CA_SLOTS;
   const int cnt_c = (int)min(*a.count_c, (uint32_t)a.P), cnt_v = (int)min(*a.count_v, (uint32_t)a.P);
@@ -131,7 +142,7 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
     const int r = q / t, cc = q - r * t;
     int sr, sc;
     pv::border_source(r, cc, n, &sr, &sc);
-    (vis ? sh.src_v : sh.src_c)[q] = (uint16_t)((sr - 1) * n + (sc - 1));
+    (vis ? src_v : src_c)[q] = (uint16_t)((sr - 1) * n + (sc - 1));
   }
   // colour interiors: items (c, i, slot, j), j fastest, so that a warp reads
   // runs of consecutive samples across neighbouring slots
@@ -150,7 +161,7 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
       }
       const uint32_t sample = a.planes_c[(size_t)c * plane + (size_t)(by * n + i) * (a.cpitch / 2) + bx * n + j];
       const uint32_t code = a.lsb ? (sample & 0x3FFu) : (sample >> 6);
-      sh.vc[s][c * T + i * n + j] = color_value(code, a.kind);
+      vc[(s * 3 + c) * T + i * n + j] = color_value(code, a.kind);
     }
   }
   // visibility interiors: an atlas row's stream bytes 12w..12w+11 (three
@@ -158,7 +169,7 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   // such chunk of one row of one run of slots within a block row, and keeps
   // the texels that belong to the block's slots
   {
-    const int n = a.nv;
+    const int n = a.nv, T = n * n;
     const size_t plane = (size_t)a.vheight * a.vpitch;
     int by = by0, bxs = bx0;                            // block of slot s0
     for (int s0 = 0; s0 < ns_v;) {
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
           const int X = 3 * w + e;
           if (X >= x_lo && X < x_hi) {
             const int so = pv::fdiv(X - x_lo, a.rcp_nv), j = X - x_lo - so * n;
-            sh.vv[s0 + so][i * n + j] = t3[e];
+            vv[(s0 + so) * T + i * n + j] = t3[e];
           }
         }
       }
@@ -194,15 +205,15 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   // probe ids: the deltas before the block's slots (block sum), and its own
   // slots' deltas (first warp: lanes 0..7 colour, lanes 8..15 visibility)
   uint32_t d = 0;
-  if (tid < 16) {
-    const int s = tid & 7;
-    const bool vis = tid >= 8;
+  if (tid < 2 * CA_SLOTS) {
+    const int s = tid & (CA_SLOTS - 1);
+    const bool vis = tid >= CA_SLOTS;
     if (s < (vis ? ns_v : ns_c)) d = vis ? a.delta_v[k0 + s] : a.delta_c[k0 + s];
   }
   sum_two(a.delta_c, ns_c ? k0 : 0, a.delta_v, ns_v ? k0 : 0, sh);   // ends in a barrier
   if (tid < 32) {
-    const int lane = tid, s = lane & 7;
-    const bool vis = lane >= 8;
+    const int lane = tid, s = lane & (CA_SLOTS - 1);
+    const bool vis = lane >= CA_SLOTS;
     const int ns = vis ? ns_v : ns_c;
     uint32_t base_c = 0, base_v = 0;
     for (int w = 0; w < CA_THREADS / 32; ++w) {
@@ -210,11 +221,11 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
       base_v += sh.red[2 * w + 1];
     }
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {                   // inclusive prefix within each group of eight
+    for (int o = 1; o < CA_SLOTS; o <<= 1) {            // inclusive prefix within each group of slots
       const uint32_t t = __shfl_up_sync(0xffffffffu, d, o);
       if (s >= o) d += t;
     }
-    if (lane < 16) {
+    if (lane < 2 * CA_SLOTS) {
       const int id = (int)(((vis ? base_v : base_c) + d) & 0xFFFFu);
       const int p = (s < ns && id < a.P) ? id : -1;
       if (vis) sh.id_v[s] = p;
@@ -226,22 +237,22 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   // whole tiles: interior and guard band, vector stores along each tile
   {
     const int T = a.nc * a.nc;
-    const auto get = [&](int s, int c, int e) { return sh.vc[s][c * T + e]; };
+    const auto get = [&](int s, int c, int e) { return vc[(s * 3 + c) * T + e]; };
     const int tt = a.tc * a.tc;
-    if (a.vw_c == 4) store_tiles<4, float4>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, sh.src_c, a.rcp_cvec, get);
-    else if (a.vw_c == 2) store_tiles<2, float2>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, sh.src_c, a.rcp_cvec, get);
-    else store_tiles<1, float>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, sh.src_c, a.rcp_cvec, get);
+    if (a.vw_c == 4) store_tiles<4, float4>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, src_c, a.rcp_cvec, get);
+    else if (a.vw_c == 2) store_tiles<2, float2>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, src_c, a.rcp_cvec, get);
+    else store_tiles<1, float>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, src_c, a.rcp_cvec, get);
   }
   {
     const auto get = [&](int s, int c, int e) {
-      const uint32_t v = sh.vv[s][e];
+      const uint32_t v = vv[s * Tv + e];
       return (uint16_t)(c ? v >> 16 : v & 0xFFFFu);
     };
     const int tt = a.tv * a.tv;
-    if (a.vw_v == 8) store_tiles<8, uint4>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, sh.src_v, a.rcp_vvec, get);
-    else if (a.vw_v == 4) store_tiles<4, uint2>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, sh.src_v, a.rcp_vvec, get);
-    else if (a.vw_v == 2) store_tiles<2, uint32_t>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, sh.src_v, a.rcp_vvec, get);
-    else store_tiles<1, uint16_t>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, sh.src_v, a.rcp_vvec, get);
+    if (a.vw_v == 8) store_tiles<8, uint4>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, src_v, a.rcp_vvec, get);
+    else if (a.vw_v == 4) store_tiles<4, uint2>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, src_v, a.rcp_vvec, get);
+    else if (a.vw_v == 2) store_tiles<2, uint32_t>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, src_v, a.rcp_vvec, get);
+    else store_tiles<1, uint16_t>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, src_v, a.rcp_vvec, get);
   }
 }
 
@@ -340,7 +351,7 @@ pv_status pv_client_apply(pv_client* c, const pv_frame* f, void* stream) {
   cudaGetDevice(&prev);
   if (prev != c->device) cudaSetDevice(c->device);
   const int blocks = (g.P + CA_SLOTS - 1) / CA_SLOTS;
-  k_client_apply<<<blocks, CA_THREADS, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+  k_client_apply<<<blocks, CA_THREADS, ca_dyn_bytes(g.nc, g.nv), reinterpret_cast<cudaStream_t>(stream)>>>(a);
   const cudaError_t e = cudaGetLastError();
   if (prev != c->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, "client apply kernel");
