@@ -401,7 +401,9 @@ pv_status pv_poll(pv_server* server, uint64_t ticket, pv_frame* out);
  *                     at or above P are skipped. Probes not in the frame
  *                     keep their tiles.
  *  pv_client_textures device pointers of the textures (owned by the client).
- * Errors: PV_ERR_INVALID (NULL frame pointer, unaligned deltas, bad desc),
+ * Errors: PV_ERR_INVALID (NULL frame pointer; deltas not 16-byte aligned,
+ * visibility planes not 4-byte, colour planes not 2-byte, counts not 4-byte
+ * aligned; bad desc),
  * PV_ERR_RANGE / PV_ERR_OOM as probe_volume_create, PV_ERR_CUDA.
  */
 typedef struct pv_client pv_client;

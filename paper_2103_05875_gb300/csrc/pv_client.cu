@@ -317,6 +317,10 @@ pv_status pv_client_apply(pv_client* c, const pv_frame* f, void* stream) {
     return pv_set_error(PV_ERR_INVALID, "pv_client_apply: frame lacks planes, deltas or device counts");
   if (((uintptr_t)f->delta_c | (uintptr_t)f->delta_v) & 15u)
     return pv_set_error(PV_ERR_INVALID, "pv_client_apply: delta buffers must be 16-byte aligned");
+  // the kernel reads 32-bit words of the visibility rows, 16-bit colour samples and 32-bit counts
+  if (((uintptr_t)f->vis_planes & 3u) || ((uintptr_t)f->color_planes & 1u) ||
+      (((uintptr_t)f->count_c_dev | (uintptr_t)f->count_v_dev) & 3u))
+    return pv_set_error(PV_ERR_INVALID, "pv_client_apply: misaligned planes or counts");
   const pv_geom& g = c->g;
   CaArgs a;
   a.P = g.P;
