@@ -69,6 +69,8 @@ def dist_setup():
         import torch.distributed as dist
         # one process per GPU over NCCL; gloo where no GPU is visible (host-side tests)
         backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)          # each rank on its own GPU before NCCL starts
         dist.init_process_group(backend=backend)
     return ws, rank, local
 
