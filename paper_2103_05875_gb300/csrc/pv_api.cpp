@@ -16,24 +16,10 @@ namespace {
 
 thread_local std::string g_last_error;
 
-size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-struct DeviceGuard {
-  int prev = -1;
-  bool changed = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
-      changed = cudaSetDevice(dev) == cudaSuccess;
-    }
-  }
-  ~DeviceGuard() {
-    if (changed) cudaSetDevice(prev);
-  }
-};
-
-pv_status cuda_fail(cudaError_t e, const char* what) {
-  return pv_set_error(PV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
+using pv_host::as_stream;
+using pv_host::cuda_fail;
+using pv_host::DeviceGuard;
+using pv_host::round_up;
 
 // Buffer sizes of a volume, computed from its descriptor alone.
 struct Layout {
@@ -147,8 +133,6 @@ Layout layout_of(const pv_desc* d) {
   L.total = off;
   return L;
 }
-
-cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 

@@ -16,23 +16,9 @@ struct pv_batch {
 
 namespace {
 
-cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
-
-pv_status cuda_fail(cudaError_t e, const char* what) {
-  return pv_set_error(PV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-class DeviceGuard {
- public:
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev_);
-    if (prev_ != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() { cudaSetDevice(prev_); }
-
- private:
-  int prev_ = 0;
-};
+using pv_host::as_stream;
+using pv_host::cuda_fail;
+using pv_host::DeviceGuard;
 
 pv_status check_members(pv_volume* const* vols, int32_t n) {
   if (!vols || n < 1) return pv_set_error(PV_ERR_INVALID, "probe_batch_create: no volumes");

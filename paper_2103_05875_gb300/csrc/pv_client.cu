@@ -256,9 +256,7 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   }
 }
 
-pv_status cuda_fail(cudaError_t e, const char* what) {
-  return pv_set_error(PV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
+using pv_host::cuda_fail;
 
 }  // namespace
 
@@ -294,12 +292,9 @@ pv_status pv_client_create(const pv_desc* d, pv_client** out) {
 
 pv_status pv_client_destroy(pv_client* c) {
   if (!c) return PV_OK;
-  int prev = 0;
-  cudaGetDevice(&prev);
-  cudaSetDevice(c->device);
+  pv_host::DeviceGuard guard(c->device);
   cudaFree(c->tex_c);
   cudaFree(c->tex_v);
-  cudaSetDevice(prev);
   delete c;
   return PV_OK;
 }
@@ -351,13 +346,10 @@ pv_status pv_client_apply(pv_client* c, const pv_frame* f, void* stream) {
   a.count_v = f->count_v_dev;
   a.tex_c = c->tex_c;
   a.tex_v = c->tex_v;
-  int prev = 0;
-  cudaGetDevice(&prev);
-  if (prev != c->device) cudaSetDevice(c->device);
+  pv_host::DeviceGuard guard(c->device);
   const int blocks = (g.P + CA_SLOTS - 1) / CA_SLOTS;
   k_client_apply<<<blocks, CA_THREADS, ca_dyn_bytes(g.nc, g.nv), reinterpret_cast<cudaStream_t>(stream)>>>(a);
   const cudaError_t e = cudaGetLastError();
-  if (prev != c->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, "client apply kernel");
   return PV_OK;
 }

@@ -154,3 +154,26 @@ cudaError_t pv_tc_batch_launch(pv_tc_batch* b, const void* const* rad, const voi
 
 // error reporting (pv_api.cpp)
 pv_status pv_set_error(pv_status s, const char* fmt, ...);
+
+// Host helpers shared by the API files.
+namespace pv_host {
+// Makes `dev` current for the guard's lifetime, then restores the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+// PV_ERR_CUDA with the message "what: CUDA error string".
+inline pv_status cuda_fail(cudaError_t e, const char* what) {
+  return pv_set_error(PV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+}  // namespace pv_host

@@ -47,17 +47,7 @@ struct Group {
   pv_batch* batch = nullptr;
 };
 
-class DeviceGuard {
- public:
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev_);
-    if (prev_ != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() { cudaSetDevice(prev_); }
-
- private:
-  int prev_ = 0;
-};
+using pv_host::DeviceGuard;
 
 bool same_shape(const pv_desc& a, const pv_desc& b) {
   return a.color_interior == b.color_interior && a.vis_interior == b.vis_interior && a.state_fmt == b.state_fmt &&

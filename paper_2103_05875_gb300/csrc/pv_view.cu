@@ -152,11 +152,9 @@ __global__ void __launch_bounds__(1024) k_view_budget(const pv_dev k, uint32_t* 
   }
 }
 
-size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+size_t up256(size_t x) { return pv_host::round_up(x, 256); }
 
-pv_status cuda_fail(cudaError_t e, const char* what) {
-  return pv_set_error(PV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
+using pv_host::cuda_fail;
 
 }  // namespace
 
@@ -168,9 +166,7 @@ pv_status pv_view_create(pv_volume* vol, pv_view** out) {
   pv_geom g;
   pv_status s = pv_frame_geometry(&vol->d, &g);
   if (s != PV_OK) return s;
-  int prev = 0;
-  cudaGetDevice(&prev);
-  if (prev != vol->device) cudaSetDevice(vol->device);
+  pv_host::DeviceGuard guard(vol->device);
   const pv_dev& vk = vol->k;
   const size_t b_lc = up256((size_t)3 * vk.P * vk.lc_stride * 2), b_lv = up256((size_t)2 * vk.P * vk.lv_stride * 2);
   const size_t b_chg = up256((size_t)2 * vk.chg_words * 4), b_idx = up256((size_t)vk.P * 2);
@@ -187,7 +183,6 @@ pv_status pv_view_create(pv_volume* vol, pv_view** out) {
     cudaFree(v->base);
     delete v;
     cudaGetLastError();
-    if (prev != vol->device) cudaSetDevice(prev);
     return pv_set_error(PV_ERR_OOM, "pv_view_create: %zu device bytes: %s", total, cudaGetErrorString(e));
   }
   v->k = vk;
@@ -221,7 +216,6 @@ pv_status pv_view_create(pv_volume* vol, pv_view** out) {
     const unsigned long long never = ~0ull;
     e = cudaMemcpy(v->k.sel_frame, &never, sizeof never, cudaMemcpyHostToDevice);
   }
-  if (prev != vol->device) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     cudaFreeHost(v->host_counts);
     cudaFree(v->base);
@@ -234,12 +228,9 @@ pv_status pv_view_create(pv_volume* vol, pv_view** out) {
 
 pv_status pv_view_destroy(pv_view* v) {
   if (!v) return PV_OK;
-  int prev = 0;
-  cudaGetDevice(&prev);
-  if (prev != v->device) cudaSetDevice(v->device);
+  pv_host::DeviceGuard guard(v->device);
   cudaFree(v->base);
   cudaFreeHost(v->host_counts);
-  if (prev != v->device) cudaSetDevice(prev);
   delete v;
   return PV_OK;
 }
@@ -254,9 +245,7 @@ pv_status pv_view_set_options(pv_view* v, const pv_view_opts* o) {
 
 pv_status pv_view_select_and_pack(pv_view* v, pv_frame* out, int32_t want_host_counts, void* stream) {
   if (!v || !out) return pv_set_error(PV_ERR_INVALID, "pv_view_select_and_pack: NULL argument");
-  int prev = 0;
-  cudaGetDevice(&prev);
-  if (prev != v->device) cudaSetDevice(v->device);
+  pv_host::DeviceGuard guard(v->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   k_view_flags<<<v->k.chg_words, VF_THREADS, 0, st>>>(v->k, v->opts.active, (uint32_t)v->opts.threshold_c,
                                                      (uint32_t)v->opts.threshold_v);
@@ -285,7 +274,6 @@ pv_status pv_view_select_and_pack(pv_view* v, pv_frame* out, int32_t want_host_c
       out->count_v = v->host_counts[1];
     }
   }
-  if (prev != v->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, "view select/pack");
   return PV_OK;
 }
