@@ -85,3 +85,30 @@ def test_select_kernel_reciprocal_division_is_exact():
     table = re.search(r"c_rcp_run\[[^\]]*\]\s*=\s*\{([^}]*)\}", src).group(1)
     vals = [int(v.strip().rstrip("u"), 16) for v in table.split(",")]
     assert vals[1:] == [((1 << 31) + d - 1) // d for d in range(1, len(vals))]
+
+
+def test_view_and_client_entry_points_reject_bad_arguments_before_any_cuda_call(built_lib):
+    """Host-side validation of the view and client entry points (no device needed)."""
+    import ctypes as C
+
+    import paper_2103_05875_gb300 as pv
+    import pv_workload as wl
+    lib = pv.lib
+    h = C.c_void_p()
+    # a description that fails validation never reaches the device
+    bad = pv.make_desc(wl.config2(), hysteresis=1.5)
+    assert lib.pv_client_create(C.byref(bad), C.byref(h)) == -1 and not h.value
+    too_big = pv.make_desc(wl.config2(), nx=64, ny=64, nz=64)
+    assert lib.pv_client_create(C.byref(too_big), C.byref(h)) == -6
+    assert lib.pv_client_create(C.byref(pv.make_desc(wl.config2())), None) == -1
+    fr = pv.pv_frame()
+    assert lib.pv_client_apply(None, C.byref(fr), None) == -1
+    assert lib.pv_client_textures(None, None, None) == -1
+    assert lib.pv_client_destroy(None) == 0
+    # views: NULL volume, NULL view, and negative knobs
+    assert lib.pv_view_create(None, C.byref(h)) == -1
+    assert lib.pv_view_select_and_pack(None, C.byref(fr), 0, None) == -1
+    opts = pv.pv_view_opts(None, 0, 0, 0)
+    assert lib.pv_view_set_options(None, C.byref(opts)) == -1
+    assert lib.pv_view_destroy(None) == 0
+    assert b"NULL" in lib.pv_last_error()
