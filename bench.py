@@ -34,8 +34,8 @@ if ROOT not in sys.path:
 NBUF = 8
 FPG = 4          # frames per captured graph in the timed replays
 # DRAM bytes (read + write) of one k_blend_tc launch of the FP32 form from one ncu capture
-# (profiles/blend_tc_16x16x16_256rays.md), valid only for the kernel source it was taken
-# on: reported as null once the source has changed.
+# of this workload, valid only for the kernel source it was taken on: reported as null once
+# the source has changed.
 BLEND_TRAFFIC = {"source_sha256_prefix": "c4839e0fa70e02d7", "f32": 27500288 + 256}
 METRIC = "probes updated+packed/sec at 16^3 probes x 256 rays (plain FP32 form)"
 UNIT = "probes/s"

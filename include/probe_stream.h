@@ -273,11 +273,16 @@ pv_status probe_volume_import_state(pv_volume* vol, const void* tiles_c, const v
  *  changed_bits           device output [2][ceil(P/32)] uint32: bit p%32 of word
  *            p/32 is set when probe p's colour (first half) or visibility
  *            (second half) codes differ from the last-transmitted ones.
- * Errors: PV_ERR_INVALID (NULL or bad field), PV_ERR_RANGE when
- * rays * (n_c^2 + n_v^2) exceeds what the scratch array holds (about 262000
- * weights), PV_ERR_CUDA. Asynchronous on `stream`. The first call on a device
- * looks up the array's device address, so make it before any stream capture.
- * All calls share the array: calls that overlap on the GPU race.
+ * Errors: PV_ERR_INVALID (NULL or bad field), PV_ERR_RANGE when the
+ * weights do not fit the scratch array: with T = n_c^2 + n_v^2 texels the
+ * array holds align256(4 R T) + align256(4 T) + 256 bytes at most, i.e.
+ * R <= (PV_STATIC_SCRATCH_BYTES - 256 - align256(4 T)) / (4 T) (1128 rays
+ * for 6x6 / 14x14 interiors, 510 for 16x16 / 16x16), PV_ERR_CUDA.
+ * Asynchronous on `stream`. The first call on a device looks up the array's
+ * device address, so make it before any stream capture; the address is kept
+ * for the life of the process, so resetting the device after that first call
+ * is not supported. All calls share the array: calls that overlap on the GPU
+ * race.
  */
 #define PV_STATIC_SCRATCH_BYTES (1u << 20)
 pv_status probe_update_static(const pv_desc* desc, uint64_t frame, const void* radiance, const void* dist,

@@ -98,7 +98,6 @@ constexpr float kD2ScaleF16 = 0.0625f;
 struct TcParams {
   pv_dev k;
   int np, items, iters, stages, kc;
-  int cluster;                           // CTAs per cluster sharing each weight chunk
   int ntiles, bufcols, nbuf;             // 128-row texel tiles; TMEM columns a buffer uses
   int vb;                                // tile row of colour texel 0 (visibility texels: rows 0..Tv-1)
   int nvc;                               // B rows (and TMEM columns) of the visibility block
@@ -197,27 +196,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void bulk_g2s_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                            uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-      "%4;" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
@@ -249,15 +232,6 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
   }
-}
-// Arrive on the barrier at `bar`'s offset in every CTA of `mask` once this
-// thread's MMAs so far have finished.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -563,7 +537,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     for (int s = 0; s < tp.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], 64);
-      mbar_init(&empty[s], tp.cluster);          // every CTA of the cluster frees the stage
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -579,8 +553,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  if (tp.cluster > 1) cluster_sync();               // peers' barriers exist before any multicast
-  else __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   // Everything above runs while the previous kernel may still be running.
@@ -590,11 +563,8 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   // and the converters touch only shared memory and TMEM. Parameter reads
   // before the wait overlap the predecessor's tail.
   int* err = k.err;
-  const uint32_t crank = tp.cluster > 1 ? cluster_rank() : 0u;
-  const uint16_t cmask = (uint16_t)((1u << tp.cluster) - 1u);
-  // rounds of this CTA: its items, or (clusters) the cluster's common count
-  const int rounds = tp.cluster > 1 ? tp.iters
-                                    : (tp.items > (int)blockIdx.x ? (tp.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
+  // rounds of this CTA: its items
+  const int rounds = tp.items > (int)blockIdx.x ? (tp.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -613,11 +583,6 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
-      // Every CTA of a cluster runs the same number of rounds (a CTA past the
-      // last item runs a round without rays, so that the weight chunks it
-      // multicasts and the stages it frees keep its peers going). Chunk kc's
-      // weight tiles are loaded once per cluster, by rank kc % cluster, into
-      // every CTA's stage.
       for (int it = 0; it < rounds && ok; ++it) {
         const int item = blockIdx.x + it * gridDim.x;
         const bool real = item < tp.items;
@@ -639,13 +604,8 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
           const uint32_t wbytes = (uint32_t)tp.ntiles * MT * ROWB;
           const uint8_t* wsrc = (const uint8_t*)bv.k.w_op + (size_t)kc * wbytes;
           const size_t wplane = (size_t)bv.k.w_chunks * wbytes;
-          if (tp.cluster == 1) {
-            bulk_g2s(st + tp.off_w, wsrc, wbytes, &full[s]);
-            if (kSplitW) bulk_g2s(st + tp.off_w_lo, wsrc + wplane, wbytes, &full[s]);
-          } else if ((uint32_t)(kc % tp.cluster) == crank) {
-            bulk_g2s_mc(st + tp.off_w, wsrc, wbytes, &full[s], cmask);
-            if (kSplitW) bulk_g2s_mc(st + tp.off_w_lo, wsrc + wplane, wbytes, &full[s], cmask);
-          }
+          bulk_g2s(st + tp.off_w, wsrc, wbytes, &full[s]);
+          if (kSplitW) bulk_g2s(st + tp.off_w_lo, wsrc + wplane, wbytes, &full[s]);
           if (++s == tp.stages) {
             s = 0;
             ph ^= 1;
@@ -668,15 +628,6 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         if (ok) {
           const BlendVol& bv = a.v[vol_of(a, blockIdx.x)];
           prefetch_item(bv.k, np, ((int)blockIdx.x - bv.item0) * np, sb, st_c, st_v, ls_c, ls_v, efull);
-        }
-      }
-      // drain: every peer's release of every stage has arrived here before the
-      // cluster may exit
-      for (int i = 0; i < tp.stages && ok && tp.cluster > 1; ++i) {
-        ok = mbar_wait(&empty[s], ph ^ 1, err);
-        if (++s == tp.stages) {
-          s = 0;
-          ph ^= 1;
         }
       }
     }
@@ -718,9 +669,8 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
               if (kSplitA) mma<FORM>(d, a, sdesc<ROWB>(st + tp.off_a_lo + brow * ROWB + kb), tp.tidesc[j], 1u);
             }
           }
-          // stage free (in every CTA of the cluster) once these MMAs finish
-          if (tp.cluster > 1) mma_commit_mc(&empty[s], cmask);
-          else mma_commit(&empty[s]);
+          // stage free once these MMAs finish
+          mma_commit(&empty[s]);
           if (++s == tp.stages) {
             s = 0;
             ph ^= 1;
@@ -959,13 +909,8 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     if (e == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
 
-  // After a timeout a peer's last weight multicast may still be in flight
-  // towards this CTA: give it time to land before the cluster may exit.
-  if (tp.cluster > 1 && *(volatile int*)err)
-    for (int i = 0; i < 64; ++i) __nanosleep(1000);
   tc_fence_before();
-  if (tp.cluster > 1) cluster_sync();               // no peer still writes into this CTA
-  else __syncthreads();
+  __syncthreads();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
@@ -1028,32 +973,6 @@ cudaError_t set_smem_attr_v(int form, int bytes) {
   return cudaFuncSetAttribute(k_blend_tc<kF32, MAXV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// Clusters of `cluster` CTAs (one CTA per SM) that fit on the GPU at once; 0
-// if the query fails.
-int max_clusters(int form, int cluster, int smem) {
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(cluster);
-  cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  cudaError_t e;
-  if (form == kF16) e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kF16, 1>, &cfg);
-  else if (form == kBF16) e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kBF16, 1>, &cfg);
-  else e = cudaOccupancyMaxActiveClusters(&n, k_blend_tc<kF32, 1>, &cfg);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
-}
-
 struct DevInfo {
   int sms, smem_max;
 };
@@ -1069,12 +988,11 @@ cudaError_t dev_info(DevInfo* d) {
 // Tile layout, stage ring and epilogue regions for volumes shaped like k, with
 // work items of at most np_want probes (fewer when shared memory demands).
 // Fills every field of tp except items, iters and the volume-dependent ones.
-cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int smem_max, bool alias_ok,
+cudaError_t make_layout(const pv_dev& k, int form, int np_want, int smem_max, bool alias_ok,
                         TcParams& tp, size_t* smem) {
   const int sb = k.state_fmt == PV_FMT_F16 ? 2 : 4;
   const int ROWB = form == kF32 ? row_bytes<kF32>() : row_bytes<kF16>();
   tp.k = k;
-  tp.cluster = cluster;
   tp.kc = k.w_kc;                              // = ROWB / operand bytes
   // ray (B) tile rows: d | d^2 (| d^2 lo, 16-bit forms) | R | G | B, 32 each
   tp.nvc = form != kF32 ? 3 * GRP : 2 * GRP;
@@ -1137,7 +1055,7 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int cluster, int
     stages = need < (size_t)smem_max ? (int)(((size_t)smem_max - need) / tp.stage_bytes) : 0;
     if (stages >= 2) break;
   }
-  if (alias_ok && cluster == 1 && stages < 3) {
+  if (alias_ok && stages < 3) {
     // One item per CTA and a shallow ring (the FP32 form): the ring takes all
     // of shared memory but the tables, and the item's old texels and codes go
     // into its first stages once the main loop no longer needs them, so the
@@ -1207,18 +1125,14 @@ cudaError_t encode_ray_maps(const pv_dev& k, int form, const TcParams& tp, const
 template <int MAXV>
 cudaError_t launch_blend(const BlendArgs<MAXV>& a, int form, int grid, size_t smem, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = a.tp.cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  attr[1] = pv_pdl_attr();
+  cudaLaunchAttribute attr[1];
+  attr[0] = pv_pdl_attr();
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = 1;
   cudaError_t e;
   if (form == kF16) e = cudaLaunchKernelEx(&cfg, k_blend_tc<kF16, MAXV>, a);
   else if (form == kBF16) e = cudaLaunchKernelEx(&cfg, k_blend_tc<kBF16, MAXV>, a);
@@ -1256,15 +1170,8 @@ bool pv_tc_supported(const pv_desc* d, const char** why) {
     if (why) *why = "rays_per_probe * operand bytes must be a multiple of 16 (TMA row pitch)";
     return false;
   }
-  int dev = 0, major = 0, minor = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  cudaGetLastError();
-  if (!(major == 10 && minor == 3)) {
-    if (why) *why = "needs an sm_103 GPU (GB300)";
-    return false;
-  }
+  // The library is built for sm_103a only, so the device needs no check
+  // here: on any other GPU no kernel of the library can launch at all.
   return true;
 }
 
@@ -1277,22 +1184,8 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   const int form = form_of(k.operand_fmt);
   e = set_smem_attr_v<1>(form, di.smem_max);
   if (e != cudaSuccess) return e;
-  // Clusters of `cluster` CTAs can share each weight chunk (multicast); the
-  // grid is the number of CTAs that can be resident at once, in whole
-  // clusters. Measured on GB300 at 16^3 probes x 256 rays, sharing gains
-  // nothing there (the MMAs, not the weight loads, bound the main loop), so
-  // one CTA per cluster is the default; PV_TC_CLUSTER=2|4|8 selects sharing.
-  int cluster = 1;
-  if (const char* env = getenv("PV_TC_CLUSTER")) {
-    const int c = atoi(env);
-    if (c == 1 || c == 2 || c == 4 || c == 8) cluster = c;
-  }
-  int resident = di.sms;
-  if (cluster > 1) {
-    const int nc = max_clusters(form, cluster, di.smem_max);
-    if (nc > 0) resident = nc * cluster;
-    else cluster = 1;
-  }
+  // one CTA per SM
+  const int resident = di.sms;
   // one item per resident CTA where possible
   const int np_max = v->state_bytes == 2 ? 32 : 16;
   int np = (k.P + resident - 1) / resident;
@@ -1302,12 +1195,11 @@ cudaError_t pv_tc_plan_create(pv_volume* v) {
   TcParams& tp = pl->args.tp;
   // a volume whose items all fit in one wave keeps each item's old tiles in
   // its CTA's stage ring (a deeper ring)
-  const bool one_wave = cluster == 1 && (k.P + np - 1) / np <= resident;
-  e = make_layout(k, form, np, cluster, di.smem_max, one_wave, tp, &pl->smem);
+  const bool one_wave = (k.P + np - 1) / np <= resident;
+  e = make_layout(k, form, np, di.smem_max, one_wave, tp, &pl->smem);
   if (e == cudaSuccess) {
     tp.items = (k.P + tp.np - 1) / tp.np;
-    const int want = (tp.items + cluster - 1) / cluster * cluster;
-    pl->grid = want < resident ? want : resident;
+    pl->grid = tp.items < resident ? tp.items : resident;
     tp.iters = (tp.items + pl->grid - 1) / pl->grid;
     if (tp.alias_stages > 0 && tp.iters != 1) e = cudaErrorInvalidConfiguration;   // cannot happen: np kept
     pl->form = form;
@@ -1361,7 +1253,7 @@ cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc
   pv_tc_batch* b = new pv_tc_batch();
   memset(b, 0, sizeof(pv_tc_batch));
   TcParams& tp = b->args.tp;
-  e = make_layout(k0, form, np, 1, di.smem_max, false, tp, &b->smem);
+  e = make_layout(k0, form, np, di.smem_max, false, tp, &b->smem);
   if (e == cudaSuccess) {
     int items = 0;
     for (int i = 0; i < n && e == cudaSuccess; ++i) {

@@ -17,7 +17,9 @@
 // In host code `g_static_scratch` is only a host-side stand-in for the device
 // array: its device address is obtained once per device with
 // cudaGetSymbolAddress (the first call on a device does this set-up, so that
-// first call should come before any stream capture).
+// first call should come before any stream capture). The address is kept for
+// the life of the process, so a device reset (cudaDeviceReset) after the first
+// call on that device is not supported.
 #include <mutex>
 
 #include "pv_internal.h"
@@ -65,13 +67,17 @@ extern "C" pv_status probe_update_static(const pv_desc* d, uint64_t frame, const
   const int P = d->nx * d->ny * d->nz, R = d->rays_per_probe;
   const int nc = d->color_interior, nv = d->vis_interior;
   const int Tc = nc * nc, Tv = nv * nv;
-  const size_t w_bytes = align256((size_t)R * (Tc + Tv) * sizeof(float));
-  const size_t need = w_bytes + align256((size_t)(Tc + Tv) * sizeof(float)) + 256;
-  if (need > PV_STATIC_SCRATCH_BYTES)
+  // scratch: R x T float weights, T float sums, 256 bytes of words, each
+  // region rounded up to 256 bytes; the most rays that fit for these texels
+  const size_t T = (size_t)(Tc + Tv);
+  const size_t w_bytes = align256((size_t)R * T * sizeof(float));
+  const size_t room = PV_STATIC_SCRATCH_BYTES - 256 - align256(T * sizeof(float));   // a multiple of 256
+  const size_t max_rays = room / (T * sizeof(float));
+  if ((size_t)R > max_rays)
     return pv_set_error(PV_ERR_RANGE,
-                        "probe_update_static: rays x texels needs %zu scratch bytes, limit %u (R*(n_c^2+n_v^2) <= %u)",
-                        need, (unsigned)PV_STATIC_SCRATCH_BYTES,
-                        (unsigned)((PV_STATIC_SCRATCH_BYTES - 4096) / sizeof(float)));
+                        "probe_update_static: %d rays per probe exceed %zu, the most the %u-byte scratch array "
+                        "holds for %zu texels (n_c^2 + n_v^2)",
+                        R, max_rays, (unsigned)PV_STATIC_SCRATCH_BYTES, T);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return pv_set_error(PV_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));

@@ -23,19 +23,31 @@ def _probe_set(bits: np.ndarray, P: int):
     return {p for p in range(P) if (b[p >> 5] >> (p & 31)) & 1}
 
 
-@pytest.mark.parametrize("state_fmt", ["f32", "f16"])
-def test_static_update_matches_volume_update_twice(state_fmt):
+# (grid, rays, interiors, state format, operand format). The 16x16 / 16x16 case uses
+# 510 rays, the most the scratch array holds for 512 texels, so the whole array is used.
+CASES = [
+    ((5, 3, 4), 64, (6, 14), "f32", "f32"),
+    ((5, 3, 4), 64, (6, 14), "f16", "f32"),
+    ((3, 2, 2), 510, (16, 16), "f16", "f32"),
+    ((5, 3, 4), 96, (6, 14), "f16", "f16"),
+]
+
+
+@pytest.mark.parametrize("grid,rays,interiors,state_fmt,operand_fmt", CASES)
+def test_static_update_matches_volume_update_twice(grid, rays, interiors, state_fmt, operand_fmt):
     pv = H.lib()
-    spec = wl.VolumeSpec(5, 3, 4, 64, state_fmt=state_fmt, operand_fmt="f32")
+    nc, nv = interiors
+    spec = wl.VolumeSpec(*grid, rays, state_fmt=state_fmt, operand_fmt=operand_fmt,
+                         color_interior=nc, vis_interior=nv)
     P = spec.probes
     W = (P + 31) // 32
     vol = pv.ProbeVolume(spec, kernel="simt")
     desc = pv.make_desc(spec)
     dt = torch.float32 if state_fmt == "f32" else torch.float16
-    tiles_c = torch.zeros((3, P, 8, 8), dtype=dt, device="cuda")
-    tiles_v = torch.zeros((2, P, 16, 16), dtype=dt, device="cuda")
-    last_c = torch.full((3, P, 36), -1, dtype=torch.int16, device="cuda")     # 0xFFFF: never sent
-    last_v = torch.full((2, P, 196), -1, dtype=torch.int16, device="cuda")
+    tiles_c = torch.zeros((3, P, nc + 2, nc + 2), dtype=dt, device="cuda")
+    tiles_v = torch.zeros((2, P, nv + 2, nv + 2), dtype=dt, device="cuda")
+    last_c = torch.full((3, P, nc * nc), -1, dtype=torch.int16, device="cuda")     # 0xFFFF: never sent
+    last_v = torch.full((2, P, nv * nv), -1, dtype=torch.int16, device="cuda")
     bits = torch.zeros(2 * W, dtype=torch.int32, device="cuda")
     fs = wl.FrameStream(spec, 77)
     for f in range(2):
@@ -64,11 +76,13 @@ def test_static_update_matches_volume_update_twice(state_fmt):
     vol.close()
 
 
-def test_static_update_rejects_sizes_beyond_its_scratch():
+@pytest.mark.parametrize("rays", [511, 1024])
+def test_static_update_rejects_sizes_beyond_its_scratch(rays):
     pv = H.lib()
-    spec = wl.VolumeSpec(2, 2, 2, 1024, color_interior=16, vis_interior=16)
+    spec = wl.VolumeSpec(2, 2, 2, rays, color_interior=16, vis_interior=16)
     desc = pv.make_desc(spec)
     z = torch.zeros(1, device="cuda")
     with pytest.raises(pv.PVError) as e:
         pv.probe_update_static(desc, 0, z, z, z, z, z, z, z, z)
     assert e.value.status == -6
+    assert "510" in str(e.value)
