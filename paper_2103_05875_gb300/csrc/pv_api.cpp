@@ -83,14 +83,14 @@ Layout layout_of(const pv_desc* d) {
   L.vheight = L.bh * L.nv;
   L.vpitch = (int)round_up((size_t)4 * ((W + 2) / 3), 16);
   // tensor-core weight images: 64-byte rows (16 FP32 or 32 16-bit weights
-  // per chunk); visibility texels in
-  // rows 0..Tv-1, colour texels from the next multiple of 8; 128-row tiles
+  // per chunk); visibility texels in rows 0..Tv-1, colour texels from the
+  // next multiple of 16 (each block is one MMA's N, a multiple of 16)
   {
     const int eb = d->operand_fmt == PV_FMT_F32 ? 4 : 2;
     L.w_rb = 64;
     L.w_kc = L.w_rb / eb;
-    L.w_vb = (int)round_up((size_t)L.Tv, 8);
-    L.w_rows = (int)round_up((size_t)L.w_vb + round_up((size_t)L.Tc, 8), 128);
+    L.w_vb = (int)round_up((size_t)L.Tv, 16);
+    L.w_rows = L.w_vb + (int)round_up((size_t)L.Tc, 16);
     L.w_chunks = (L.R + L.w_kc - 1) / L.w_kc;
   }
   L.sb = d->state_fmt == PV_FMT_F16 ? 2 : 4;

@@ -29,8 +29,6 @@ pv_status check_members(pv_volume* const* vols, int32_t n) {
       if (vols[j] == vols[i]) return pv_set_error(PV_ERR_INVALID, "probe_batch_create: volume %d listed twice", i);
     const pv_desc& a = vols[0]->d;
     const pv_desc& b = vols[i]->d;
-    if (vols[i]->kernel != PV_KERNEL_TCGEN05)
-      return pv_set_error(PV_ERR_UNSUPPORTED, "probe_batch_create: volume %d does not use the tensor-core blend", i);
     if (vols[i]->device != vols[0]->device)
       return pv_set_error(PV_ERR_INVALID, "probe_batch_create: volumes on different devices");
     if (a.color_interior != b.color_interior || a.vis_interior != b.vis_interior || a.state_fmt != b.state_fmt ||
@@ -39,6 +37,8 @@ pv_status check_members(pv_volume* const* vols, int32_t n) {
                           "probe_batch_create: volume %d differs in tile interiors, state or operand format, or "
                           "colour code",
                           i);
+    if (vols[i]->kernel != PV_KERNEL_TCGEN05)
+      return pv_set_error(PV_ERR_UNSUPPORTED, "probe_batch_create: volume %d does not use the tensor-core blend", i);
   }
   return PV_OK;
 }
