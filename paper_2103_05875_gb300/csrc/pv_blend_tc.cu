@@ -15,7 +15,7 @@
 //     split them into TF32 hi + lo parts held in tensor memory (A from TMEM,
 //     so the MMAs read only the weights from shared memory). 16-bit forms:
 //     A is the TMA tile itself in shared memory; d^2 = hi + lo is formed on
-//     chip, with the lo part in a second A tile whose d lanes are zero.
+//     chip, the lo part in a second A tile whose d lanes are zero.
 //   B (texels, K-major): the weights kernel writes each K chunk as the exact
 //     swizzled shared-memory image of [visibility texels | colour texels],
 //     each block padded to 16 rows, so a chunk's block arrives with one bulk
@@ -51,8 +51,10 @@
 // codes as soon as this item's are written back.
 //
 // Warp roles (512 threads, one CTA per SM, persistent over work items):
-//   warp 0      producer: ray tiles (TMA) and weight images (bulk copies)
-//   warp 1      TMEM allocation and the single MMA-issuing thread
+//   warp 0      ray producer (TMA), running ahead from the kernel's start
+//   warp 1      TMEM allocation
+//   warp 2      weight producer (bulk copies of the weight tile images)
+//   warp 3      the single MMA-issuing thread
 //   warps 4-7   converters (lane quarter = warp % 4): TF32 split into TMEM
 //               (F32), d^2 hi + lo into shared memory (16-bit forms)
 //   warps 8-15  epilogue, two per lane quarter
@@ -81,7 +83,6 @@ constexpr int NT = 512;
 constexpr int ROWB = 64;                 // bytes per K-chunk row (SWIZZLE_64B): 16 FP32 or 32 16-bit rays
 constexpr int QROWS = 32;                // probe rows per lane quarter
 constexpr int A_BYTES = 128 * ROWB;      // one 128-row A tile of a stage
-constexpr int kMaxStages = 6;
 constexpr int EPI_THREADS = 256;         // warps 8..15
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 // binary16 operand form: d^2 enters the MMA scaled by 2^-4 (exact), which
@@ -102,20 +103,23 @@ struct Shape {
 
 struct TcParams {
   pv_dev k;                              // shapes and formats shared by the volumes of the launch
-  int np, items, stages, kc;             // probes per item, items, ring depth, rays per chunk
-  int stage_bytes;
-  int off_x, off_xlo, off_w, off_wlo;    // within a stage: A (or ray) tile, A lo tile, weight planes
-  int off_tv, off_lv, off_tc, off_lc;    // epilogue boxes: visibility tiles / codes, colour tiles / codes
-  int boxb;                              // bytes reserved per box (np rows of 128 bytes, 1024-aligned)
+  int np, items, kc;                     // probes per item, items, rays per chunk
+  int xs, ws, as_;                       // ring depths: ray tiles, weight tiles, F32 TMEM A tiles
+  int xstage, wstage;                    // bytes per ray stage (A tile [+ lo A tile]) and weight stage
+  int off_xr, off_wr;                    // the two rings
+  int off_tv, off_lv, off_tc, off_lc;    // epilogue regions: visibility tiles / codes, colour tiles / codes
+  int boxb;                              // bytes reserved per tile box (np rows of 128 bytes, 1024-aligned)
+  int lreg_v, lreg_c;                    // bytes reserved per channel of code rows (np dense rows)
   int off_cf, off_km, off_bar;           // tables, barriers
-  uint32_t tx_v, tx_c;                   // bytes per stage of the visibility / colour phase
+  uint32_t tx_xv, tx_xc, tx_wv, tx_wc;   // bytes per ray / weight stage, visibility / colour phase
   uint32_t idesc_v, idesc_c, idesc_c2;   // instruction descriptors (N = NVP, NCP, 2 NCP)
   int abase;                             // F32: first TMEM column of the A ring (32 columns per stage)
 };
 
 // One volume of a launch: its tensor maps, its buffers and its work items.
-// The epilogue moves texels and codes with 3-D maps [channel][probe][row]
-// whose boxes are 128-byte column strips of np probe rows (SWIZZLE_128B).
+// The epilogue moves texels and codes with 3-D maps [channel][probe][row]:
+// texels in boxes of 128-byte column strips of np probe rows (SWIZZLE_128B),
+// codes in one box of np whole rows.
 struct BlendVol {
   CUtensorMap rad, dist;                 // this frame's rays
   CUtensorMap st_v, st_c;                // state tiles (read and written)
@@ -374,47 +378,50 @@ __device__ __forceinline__ uint32_t texel_code(uint32_t b) {
   }
 }
 
-// Interior row i of this thread's probe row: new stored bits nb[j] and the
-// transmitted codes in pairs cw[m] = code(2m) | code(2m+1) << 16.
-//   tm      TMEM address of this lane's accumulator of texel (i, 0)
-//   tb, ti  this thread's tile row in the box set, and the tile row i + 1 (old texels)
-//   s_cf    shared address of the row's factors (1 - h) * scale / S per texel
-//   km      texels of the row whose weight sum is 0 (bit j): they keep their value
-//   tsplit  > 0: the accumulator is split over two column blocks this far
-//           apart (the weights' hi and lo parts), which are added
-template <int N, int SB, int KIND, bool VIS>
-__device__ __forceinline__ void update_row(uint32_t tm, uint32_t tsplit, const BoxRow& tb, int ti, uint32_t s_cf,
-                                           uint32_t km, float h, uint32_t (&nb)[N], uint32_t (&cw)[N / 2]) {
+// Loads of interior row i of this thread's probe row, issued without waiting:
+// its accumulators (TMEM; with tsplit > 0 also the second column block this
+// far apart, the weights' lo part, which is added) and its old tile row i + 1.
+template <int N, int SB>
+struct RowIn {
+  float acc[N], lo[N];
+  uint32_t w[(N + 2) * SB / 4];
+};
+template <int N, int SB>
+__device__ __forceinline__ void load_row(uint32_t tm, uint32_t tsplit, const BoxRow& tb, int ti, RowIn<N, SB>& r) {
   constexpr int RW = (N + 2) * SB / 4;
-  constexpr int RP = round_up_c(N, 4);
-  float acc[N];
 #pragma unroll
-  for (int m = 0; m < N / 2; ++m) tmem_ld2(tm + 2u * m, acc[2 * m], acc[2 * m + 1]);
+  for (int m = 0; m < N / 2; ++m) tmem_ld2(tm + 2u * m, r.acc[2 * m], r.acc[2 * m + 1]);
   if (tsplit) {
-    float lo[N];
 #pragma unroll
-    for (int m = 0; m < N / 2; ++m) tmem_ld2(tm + tsplit + 2u * m, lo[2 * m], lo[2 * m + 1]);
-    tmem_wait_ld();
-#pragma unroll
-    for (int j = 0; j < N; ++j) acc[j] += lo[j];
+    for (int m = 0; m < N / 2; ++m) tmem_ld2(tm + tsplit + 2u * m, r.lo[2 * m], r.lo[2 * m + 1]);
   }
-  uint32_t w[RW];
 #pragma unroll
   for (int c = 0; c < RW / 4; ++c)
-    lds128(at(tb, (uint32_t)ti * (RW * 4) + 16u * c), w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+    lds128(at(tb, (uint32_t)ti * (RW * 4) + 16u * c), r.w[4 * c], r.w[4 * c + 1], r.w[4 * c + 2], r.w[4 * c + 3]);
+}
+
+// Interior row i once its loads completed: new stored bits nb[j] and the
+// transmitted codes in pairs cw[m] = code(2m) | code(2m+1) << 16.
+//   s_cf    shared address of the row's factors (1 - h) * scale / S per texel
+//   km      texels of the row whose weight sum is 0 (bit j): they keep their value
+template <int N, int SB, int KIND, bool VIS>
+__device__ __forceinline__ void finish_row(RowIn<N, SB>& r, bool split, uint32_t s_cf, uint32_t km, float h,
+                                           uint32_t (&nb)[N], uint32_t (&cw)[N / 2]) {
+  constexpr int RW = (N + 2) * SB / 4;
+  constexpr int RP = round_up_c(N, 4);
   float cf[RP];
 #pragma unroll
   for (int c = 0; c < RP / 4; ++c) lds128f(s_cf + 16u * c, cf[4 * c], cf[4 * c + 1], cf[4 * c + 2], cf[4 * c + 3]);
-  tmem_wait_ld();
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    const float of = state_value<SB>(row_el<SB, RW>(w, j + 1));
-    nb[j] = state_bits<SB>(fmaf(h, of, acc[j] * cf[j]));
+    const float acc = split ? r.acc[j] + r.lo[j] : r.acc[j];
+    const float of = state_value<SB>(row_el<SB, RW>(r.w, j + 1));
+    nb[j] = state_bits<SB>(fmaf(h, of, acc * cf[j]));
   }
   if (km) {                                          // rare: texels without any weight
 #pragma unroll
     for (int j = 0; j < N; ++j)
-      if ((km >> j) & 1u) nb[j] = row_el<SB, RW>(w, j + 1);
+      if ((km >> j) & 1u) nb[j] = row_el<SB, RW>(r.w, j + 1);
   }
 #pragma unroll
   for (int m = 0; m < N / 2; ++m)
@@ -452,27 +459,34 @@ __device__ __forceinline__ void store_row(bool on, const BoxRow& tb, int ti, uin
 // and returns whether any code differs from the last transmitted one.
 template <int N, int SB, int KIND, bool VIS>
 __device__ __forceinline__ bool update_pair(bool on, int i, uint32_t tm0, uint32_t tsplit, const BoxRow& tb,
-                                            const BoxRow& cb, uint32_t s_cf, uint32_t s_km, float h) {
+                                            uint32_t cb, uint32_t s_cf, uint32_t s_km, float h) {
   constexpr int RP = round_up_c(N, 4);
   const int i2 = N - 1 - i;
+  const uint32_t qa = 2u * N * i, qb = 2u * N * i2;  // code row offsets of the two rows
+  // every load of both rows first (one TMEM wait for the pair), then the arithmetic
+  RowIn<N, SB> ra, rb;
+  load_row<N, SB>(tm0 + (uint32_t)(N * i), tsplit, tb, i + 1, ra);
+  load_row<N, SB>(tm0 + (uint32_t)(N * i2), tsplit, tb, i2 + 1, rb);
+  uint32_t la[N / 2], lb[N / 2];
+#pragma unroll
+  for (int m = 0; m < N / 2; ++m) {
+    la[m] = lds32(cb + qa + 4u * m);
+    lb[m] = lds32(cb + qb + 4u * m);
+  }
+  const uint32_t kma = lds32(s_km + 4u * i), kmb = lds32(s_km + 4u * i2);
+  tmem_wait_ld();
   uint32_t a[N], b[N], ca[N / 2], cc[N / 2];
-  update_row<N, SB, KIND, VIS>(tm0 + (uint32_t)(N * i), tsplit, tb, i + 1, s_cf + 4u * RP * i, lds32(s_km + 4u * i),
-                               h, a, ca);
-  update_row<N, SB, KIND, VIS>(tm0 + (uint32_t)(N * i2), tsplit, tb, i2 + 1, s_cf + 4u * RP * i2,
-                               lds32(s_km + 4u * i2), h, b, cc);
+  finish_row<N, SB, KIND, VIS>(ra, tsplit != 0, s_cf + 4u * RP * i, kma, h, a, ca);
+  finish_row<N, SB, KIND, VIS>(rb, tsplit != 0, s_cf + 4u * RP * i2, kmb, h, b, cc);
   // codes of both rows against the last transmitted ones; the code row then
   // holds the current codes (which select/pack sends)
   uint32_t diff = 0;
-  const uint32_t qa = 2u * N * i, qb = 2u * N * i2;
+#pragma unroll
+  for (int m = 0; m < N / 2; ++m) diff |= (la[m] ^ ca[m]) | (lb[m] ^ cc[m]);
 #pragma unroll
   for (int m = 0; m < N / 2; ++m) {
-    diff |= lds32(at(cb, qa + 4u * m)) ^ ca[m];
-    diff |= lds32(at(cb, qb + 4u * m)) ^ cc[m];
-  }
-#pragma unroll
-  for (int m = 0; m < N / 2; ++m) {
-    sts32_if(on, at(cb, qa + 4u * m), ca[m]);
-    sts32_if(on, at(cb, qb + 4u * m), cc[m]);
+    sts32_if(on, cb + qa + 4u * m, ca[m]);
+    sts32_if(on, cb + qb + 4u * m, cc[m]);
   }
   store_row<N, SB>(on, tb, i + 1, b[0], a, b[N - 1]);
   store_row<N, SB>(on, tb, i2 + 1, a[0], b, a[N - 1]);
@@ -493,7 +507,7 @@ __device__ __forceinline__ bool update_pair(bool on, int i, uint32_t tm0, uint32
 // its slot (p % 2 == slot). Returns whether any code of the row changed.
 template <int N, int SB, int KIND, bool VIS>
 __device__ __forceinline__ bool epi_rows(bool on, int slot, uint32_t tm0, uint32_t tsplit, const BoxRow& tb,
-                                         const BoxRow& cb, uint32_t s_cf, uint32_t s_km, float h) {
+                                         uint32_t cb, uint32_t s_cf, uint32_t s_km, float h) {
   bool ch = false;
 #pragma unroll 1
   for (int p = slot; p < N / 2; p += 2) ch |= update_pair<N, SB, KIND, VIS>(on, p, tm0, tsplit, tb, cb, s_cf, s_km, h);
@@ -510,28 +524,42 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   const TcParams& tp = a.tp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool kSplitW = FORM != kF16;
+  constexpr bool kTmemA = FORM == kF32;
+  constexpr bool kD2Lo = FORM != kF32;               // 16-bit forms: d^2 as hi + lo
   constexpr uint32_t TBV = (uint32_t)((NV + 2) * (NV + 2) * SB), TBC = (uint32_t)((NC + 2) * (NC + 2) * SB);
+  constexpr uint32_t WLO_V = (uint32_t)S::NVP * ROWB;              // visibility lo plane offset in a weight stage
 
-  uint64_t* bars = (uint64_t*)(smem + tp.off_bar);
-  uint64_t* full = bars;                           // [stages]
-  uint64_t* conv = bars + tp.stages;               // [stages]
-  uint64_t* empty = bars + 2 * tp.stages;          // [stages]
-  uint64_t* tfull = bars + 3 * tp.stages;          // [2]: visibility, colour accumulators ready
-  uint64_t* tempty = tfull + 2;                    // [2]: accumulators drained
-  uint64_t* efull = tempty + 2;                    // [2]: an item's old texels and codes arrived
+  uint64_t* xfull = (uint64_t*)(smem + tp.off_bar);  // [xs] ray tiles landed
+  uint64_t* xconv = xfull + tp.xs;                   // [xs] 16-bit forms: d^2 parts written
+  uint64_t* xempty = xconv + tp.xs;                  // [xs] ray stage free
+  uint64_t* wfull = xempty + tp.xs;                  // [ws] weight tiles landed
+  uint64_t* wempty = wfull + tp.ws;                  // [ws] weight stage free
+  uint64_t* afull = wempty + tp.ws;                  // [as] F32: TMEM A stage written
+  uint64_t* aempty = afull + tp.as_;                 // [as] F32: TMEM A stage free
+  uint64_t* tfull = aempty + tp.as_;                 // [2] visibility, colour accumulators ready
+  uint64_t* tempty = tfull + 2;                      // [2] accumulators drained
+  uint64_t* efull = tempty + 2;                      // [2] an item's old texels and codes arrived
   uint32_t* tmem_holder = (uint32_t*)(efull + 2);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < tp.stages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 4);                      // the four converter warps
-      mbar_init(&empty[s], 1);
+    for (int i = 0; i < tp.xs; ++i) {
+      mbar_init(&xfull[i], 1);
+      mbar_init(&xconv[i], 4);                       // the four converter warps
+      mbar_init(&xempty[i], kTmemA ? 4 : 1);         // converters (F32) or the MMAs (16-bit)
+    }
+    for (int i = 0; i < tp.ws; ++i) {
+      mbar_init(&wfull[i], 1);
+      mbar_init(&wempty[i], 1);
+    }
+    for (int i = 0; i < tp.as_; ++i) {
+      mbar_init(&afull[i], 4);
+      mbar_init(&aempty[i], 1);
     }
     for (int b = 0; b < 2; ++b) mbar_init(&tfull[b], 1);
-    mbar_init(&efull[0], 2);                       // one loading thread per visibility channel
-    mbar_init(&efull[1], 3);                       // and per colour channel
-    mbar_init(&tempty[0], 4);                      // visibility epilogue warps (quarters 0, 1)
-    mbar_init(&tempty[1], 6);                      // colour epilogue warps (quarters 1, 2, 3)
+    mbar_init(&tempty[0], 4);                        // visibility epilogue warps (quarters 0, 1)
+    mbar_init(&tempty[1], 6);                        // colour epilogue warps (quarters 1, 2, 3)
+    mbar_init(&efull[0], 2);                         // one loading thread per visibility channel
+    mbar_init(&efull[1], 3);                         // and per colour channel
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -547,54 +575,23 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   int* err = tp.k.err;
   const int np = tp.np;
   const int rounds = tp.items > (int)blockIdx.x ? (tp.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  uint8_t* xring = smem + tp.off_xr;
+  uint8_t* wring = smem + tp.off_wr;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------------------ ray producer
+    // The rays are this frame's inputs, complete before the weights kernel
+    // started, so their tiles stream in from the kernel's start, as far
+    // ahead of the MMAs as the ray ring allows (no wait for the previous
+    // kernel). Visibility chunk: d rows into lane quarter 0; colour chunk:
+    // R, G, B rows into quarters 1..3.
     if (lane == 0) {
       for (int v = 0; v < a.nvol; ++v) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].dist) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].rad) : "memory");
       }
-      const uint32_t wvb = (uint32_t)S::NVP * ROWB, wcb = (uint32_t)S::NCP * ROWB;
-      // chunk kc of a phase: the ray tiles (visibility: d rows into lane
-      // quarter 0; colour: R, G, B rows into quarters 1..3), then the weight
-      // tile image(s) of that phase's texels
-      auto issue_x = [&](int s, const BlendVol& bv, int phase, int kc, int p0) {
-        uint8_t* st = smem + (size_t)s * tp.stage_bytes;
-        const int x = kc * tp.kc;
-        if (phase == 0) {
-          tma_load_2d(st + tp.off_x, &bv.dist, x, p0, &full[s]);
-        } else {
-          for (int c = 0; c < 3; ++c)
-            tma_load_2d(st + tp.off_x + (c + 1) * QROWS * ROWB, &bv.rad, x, c * bv.k.P + p0, &full[s]);
-        }
-      };
-      auto issue_w = [&](int s, const BlendVol& bv, int phase, int kc) {
-        uint8_t* st = smem + (size_t)s * tp.stage_bytes;
-        const size_t chunk_b = (size_t)bv.k.w_rows * ROWB;
-        const size_t plane_b = (size_t)bv.k.w_chunks * chunk_b;
-        const uint8_t* wsrc = (const uint8_t*)bv.k.w_op + (size_t)kc * chunk_b + (phase == 0 ? 0 : wvb);
-        const uint32_t wb = phase == 0 ? wvb : wcb;
-        bulk_g2s(smem_u32(st + tp.off_w), wsrc, wb, &full[s]);
-        // colour: the lo rows right after the hi rows, so that one MMA of
-        // N = 2 NCP takes both parts of the weights
-        if (kSplitW) bulk_g2s(smem_u32(st + (phase == 0 ? tp.off_wlo : tp.off_w + (int)wcb)), wsrc + plane_b, wb, &full[s]);
-      };
-      // The rays are this frame's inputs, complete before the weights kernel
-      // started, so the first stages' ray tiles go out before the wait for
-      // the previous kernel; their weight tiles (which it writes) after it.
-      const BlendVol& b0 = a.v[vol_of(a, blockIdx.x)];
-      const int p00 = ((int)blockIdx.x - b0.item0) * np;
-      const int pre = rounds > 0 ? min(tp.stages, 2 * b0.nchunks) : 0;
-      for (int j = 0; j < pre; ++j) {
-        const int phase = j / b0.nchunks, kc = j % b0.nchunks;
-        mbar_expect_tx(&full[j], phase == 0 ? tp.tx_v : tp.tx_c);
-        issue_x(j, b0, phase, kc, p00);
-      }
-      pv_grid_wait();
-      for (int j = 0; j < pre; ++j) issue_w(j, b0, j / b0.nchunks, j % b0.nchunks);
-      int s = pre == tp.stages ? 0 : pre;
-      uint32_t ph = pre == tp.stages ? 1u : 0u;
+      int x = 0;
+      uint32_t ph = 0;
       bool ok = true;
       for (int it = 0; it < rounds && ok; ++it) {
         const int item = blockIdx.x + it * gridDim.x;
@@ -602,25 +599,67 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         const int p0 = (item - bv.item0) * np;
         for (int phase = 0; phase < 2 && ok; ++phase) {
           for (int kc = 0; kc < bv.nchunks; ++kc) {
-            if (it == 0 && phase * bv.nchunks + kc < pre) continue;   // issued above
-            ok = mbar_wait(&empty[s], ph ^ 1, err);
+            ok = mbar_wait(&xempty[x], ph ^ 1, err);
             if (!ok) break;
-            mbar_expect_tx(&full[s], phase == 0 ? tp.tx_v : tp.tx_c);
-            issue_x(s, bv, phase, kc, p0);
-            issue_w(s, bv, phase, kc);
-            if (++s == tp.stages) {
-              s = 0;
+            uint8_t* st = xring + (size_t)x * tp.xstage;
+            const int xr = kc * tp.kc;
+            if (phase == 0) {
+              mbar_expect_tx(&xfull[x], tp.tx_xv);
+              tma_load_2d(st, &bv.dist, xr, p0, &xfull[x]);
+            } else {
+              mbar_expect_tx(&xfull[x], tp.tx_xc);
+              for (int c = 0; c < 3; ++c)
+                tma_load_2d(st + (c + 1) * QROWS * ROWB, &bv.rad, xr, c * bv.k.P + p0, &xfull[x]);
+            }
+            if (++x == tp.xs) {
+              x = 0;
               ph ^= 1;
             }
           }
         }
       }
     }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+  } else if (warp == 2) {
+    // ------------------------------------------------------------ weight producer
+    // The weight tile images (written by the weights kernel): visibility
+    // chunk hi rows then lo rows; colour chunk hi then lo rows adjacent, so
+    // that one MMA of N = 2 NCP takes both parts.
     if (lane == 0) {
-      int s = 0;
-      uint32_t ph = 0, tph[2] = {0u, 0u};
+      pv_grid_wait();
+      const uint32_t wvb = (uint32_t)S::NVP * ROWB, wcb = (uint32_t)S::NCP * ROWB;
+      int w = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int it = 0; it < rounds && ok; ++it) {
+        const int item = blockIdx.x + it * gridDim.x;
+        const BlendVol& bv = a.v[vol_of(a, item)];
+        const size_t chunk_b = (size_t)bv.k.w_rows * ROWB;
+        const size_t plane_b = (size_t)bv.k.w_chunks * chunk_b;
+        for (int phase = 0; phase < 2 && ok; ++phase) {
+          for (int kc = 0; kc < bv.nchunks; ++kc) {
+            ok = mbar_wait(&wempty[w], ph ^ 1, err);
+            if (!ok) break;
+            const uint32_t st = smem_u32(wring + (size_t)w * tp.wstage);
+            const uint8_t* src = (const uint8_t*)bv.k.w_op + (size_t)kc * chunk_b + (phase == 0 ? 0 : wvb);
+            const uint32_t wb = phase == 0 ? wvb : wcb;
+            mbar_expect_tx(&wfull[w], phase == 0 ? tp.tx_wv : tp.tx_wc);
+            bulk_g2s(st, src, wb, &wfull[w]);
+            if (kSplitW) bulk_g2s(st + wb, src + plane_b, wb, &wfull[w]);
+            if (++w == tp.ws) {
+              w = 0;
+              ph ^= 1;
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 3) {
+    // ------------------------------------------------------------ MMA issuer
+    // (on the fourth SMSP, which the visibility epilogue does not use)
+    if (lane == 0) {
+      int x = 0, w = 0, sa = 0;
+      uint32_t xph = 0, wph = 0, aph = 0, tph[2] = {0u, 0u};
+      uint32_t cvph = 0;                             // 16-bit: next d^2 phase parity per ray stage (bit x)
       bool ok = true;
       for (int it = 0; it < rounds && ok; ++it) {
         const int item = blockIdx.x + it * gridDim.x;
@@ -632,39 +671,61 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
           const uint32_t d = tmem + (phase == 0 ? 0u : (uint32_t)S::CBASE);
           const uint32_t idesc = phase == 0 ? tp.idesc_v : tp.idesc_c;
           for (int kc = 0; kc < nchunks; ++kc) {
-            ok = mbar_wait(&conv[s], ph, err);            // the converters saw the stage full
+            // ray tiles ready: F32 in TMEM (converters); 16-bit visibility
+            // chunks once d^2 is written, colour chunks as soon as they land
+            if (kTmemA) {
+              ok = mbar_wait(&afull[sa], aph, err);
+            } else if (phase == 0) {
+              ok = mbar_wait(&xconv[x], (cvph >> x) & 1u, err);
+              cvph ^= 1u << x;
+            } else {
+              ok = mbar_wait(&xfull[x], xph, err);
+            }
+            if (ok) ok = mbar_wait(&wfull[w], wph, err);
             if (!ok) break;
             tc_fence_after();
-            const uint32_t st = smem_u32(smem + (size_t)s * tp.stage_bytes);
+            const uint32_t wb = smem_u32(wring + (size_t)w * tp.wstage);
+            const uint32_t xa = smem_u32(xring + (size_t)x * tp.xstage);
 #pragma unroll
             for (int ks = 0; ks < ROWB / 32; ++ks) {            // one MMA K step per 32 bytes of row
               const uint32_t kb = 32u * ks;
               const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-              const uint64_t bw = sdesc(st + tp.off_w + kb);
-              if constexpr (FORM == kF32) {
-                const uint32_t ah = tmem + (uint32_t)tp.abase + 32u * s + 8u * ks;
+              const uint64_t bw = sdesc(wb + kb);
+              if constexpr (kTmemA) {
+                const uint32_t ah = tmem + (uint32_t)tp.abase + 32u * sa + 8u * ks;
                 if (phase == 0) {
                   mma_ts_tf32(d, ah, bw, idesc, acc);                          // hi * hi
-                  mma_ts_tf32(d, ah, sdesc(st + tp.off_wlo + kb), idesc, 1u);  // hi * lo
+                  mma_ts_tf32(d, ah, sdesc(wb + WLO_V + kb), idesc, 1u);       // hi * lo
                 } else {
                   mma_ts_tf32(d, ah, bw, tp.idesc_c2, acc);                    // hi * [hi | lo]
                 }
                 mma_ts_tf32(d, ah + 16u, bw, idesc, 1u);                       // lo * hi
               } else {
-                const uint64_t ax = sdesc(st + tp.off_x + kb);
+                const uint64_t ax = sdesc(xa + kb);
                 if (kSplitW && phase == 1) {
                   mma_ss<FORM>(d, ax, bw, tp.idesc_c2, acc);                   // x * [hi | lo]
                 } else {
                   mma_ss<FORM>(d, ax, bw, idesc, acc);
-                  if (kSplitW) mma_ss<FORM>(d, ax, sdesc(st + tp.off_wlo + kb), idesc, 1u);
+                  if (kSplitW) mma_ss<FORM>(d, ax, sdesc(wb + WLO_V + kb), idesc, 1u);
                 }
-                if (phase == 0) mma_ss<FORM>(d, sdesc(st + tp.off_xlo + kb), bw, idesc, 1u);   // d^2 lo
+                if (kD2Lo && phase == 0) mma_ss<FORM>(d, sdesc(xa + A_BYTES + kb), bw, idesc, 1u);   // d^2 lo
               }
             }
-            mma_commit(&empty[s]);                               // stage free once these MMAs finish
-            if (++s == tp.stages) {
-              s = 0;
-              ph ^= 1;
+            // stages free once these MMAs finish
+            if constexpr (kTmemA) mma_commit(&aempty[sa]);
+            else mma_commit(&xempty[x]);
+            mma_commit(&wempty[w]);
+            if (++x == tp.xs) {
+              x = 0;
+              xph ^= 1;
+            }
+            if (++w == tp.ws) {
+              w = 0;
+              wph ^= 1;
+            }
+            if (kTmemA && ++sa == tp.as_) {
+              sa = 0;
+              aph ^= 1;
             }
           }
           if (!ok) break;
@@ -676,30 +737,39 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   } else if (warp >= 4 && warp < 8) {
     // ------------------------------------------------------------ converters
     const int q = warp & 3;
-    uint8_t* base = smem;
-    if constexpr (FORM != kF32) {
+    if constexpr (kD2Lo) {
       // the lo A tile's visibility d lanes stay zero: its MMA adds d^2 lo only
       if (q == 0)
-        for (int s = 0; s < tp.stages; ++s)
+        for (int s = 0; s < tp.xs; ++s)
           for (int o = lane * 16; o < QROWS * ROWB; o += 32 * 16)
-            *(uint4*)(base + (size_t)s * tp.stage_bytes + tp.off_xlo + o) = make_uint4(0u, 0u, 0u, 0u);
+            *(uint4*)(xring + (size_t)s * tp.xstage + A_BYTES + o) = make_uint4(0u, 0u, 0u, 0u);
       fence_proxy_async();
     }
-    int s = 0;
-    uint32_t ph = 0;
+    int x = 0, sa = 0;
+    uint32_t ph = 0, aph = 0;
     bool ok = true;
     for (int it = 0; it < rounds && ok; ++it) {
       const int item = blockIdx.x + it * gridDim.x;
       const int nchunks = a.v[vol_of(a, item)].nchunks;
       for (int phase = 0; phase < 2 && ok; ++phase) {
+        if (!kTmemA && phase == 1) {                 // 16-bit colour chunks need no conversion
+          x += nchunks;
+          while (x >= tp.xs) {
+            x -= tp.xs;
+            ph ^= 1;
+          }
+          continue;
+        }
         for (int kc = 0; kc < nchunks; ++kc) {
-          ok = mbar_wait(&full[s], ph, err);
+          ok = mbar_wait(&xfull[x], ph, err);
           if (!ok) break;
-          uint8_t* st = base + (size_t)s * tp.stage_bytes;
-          const uint32_t sx = smem_u32(st + tp.off_x);
-          if constexpr (FORM == kF32) {
+          const uint32_t sx = smem_u32(xring + (size_t)x * tp.xstage);
+          if constexpr (kTmemA) {
             // my lane quarter's rows: visibility q0 = d, q1 = d^2 (from d);
             // colour q1..q3 = R, G, B; each split into TF32 hi + lo in TMEM
+            ok = mbar_wait(&aempty[sa], aph ^ 1, err);
+            if (!ok) break;
+            tc_fence_after();
             const bool work = phase == 0 ? q <= 1 : q >= 1;
             if (work) {
               const int row = phase == 0 ? lane : 32 * q + lane;
@@ -719,19 +789,28 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
                   lo[4 * u + e] = __float_as_uint(v - __uint_as_float(h));
                 }
               }
-              const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)tp.abase + 32u * s;
+              const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)tp.abase + 32u * sa;
               tmem_st16(ta, hi);
               tmem_st16(ta + 16u, lo);
               tmem_wait_st();
             }
             tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+              mbar_arrive(&afull[sa]);
+              mbar_arrive(&xempty[x]);
+            }
+            if (++sa == tp.as_) {
+              sa = 0;
+              aph ^= 1;
+            }
           } else {
             // d^2 = hi + lo in the operand format (binary16 scaled by 2^-4):
             // the hi part into lane quarter 1 of the A tile, the lo part into
             // lane quarter 1 of the lo A tile; converter warp q takes 16-byte
             // unit q of every d row (8 rays), so the four share each chunk
             if (phase == 0) {
-              const uint32_t sxl = smem_u32(st + tp.off_xlo);
+              const uint32_t sxl = sx + A_BYTES;
               const int u = q;
               uint32_t r[4];
               lds128(sx + swz64(lane, u), r[0], r[1], r[2], r[3]);
@@ -762,16 +841,17 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
               asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + o), "r"(oh[0]), "r"(oh[1]), "r"(oh[2]),
                            "r"(oh[3])
                            : "memory");
-              asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sxl + o), "r"(ol[0]), "r"(ol[1]), "r"(ol[2]),
-                           "r"(ol[3])
-                           : "memory");
+              if (kD2Lo)
+                asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sxl + o), "r"(ol[0]), "r"(ol[1]),
+                             "r"(ol[2]), "r"(ol[3])
+                             : "memory");
               fence_proxy_async();
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xconv[x]);
           }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&conv[s]);
-          if (++s == tp.stages) {
-            s = 0;
+          if (++x == tp.xs) {
+            x = 0;
             ph ^= 1;
           }
         }
@@ -792,25 +872,25 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     const uint32_t boxb = (uint32_t)tp.boxb;
     // boxes per probe row: tiles (128 bytes of texels each), codes (64 codes each)
     constexpr int BTV = (int)(TBV / 128), BTC = (int)(TBC / 128);
-    const int bcv = (tp.k.lv_stride + 63) / 64, bcc = (tp.k.lc_stride + 63) / 64;
+    const uint32_t lsv = (uint32_t)tp.k.lv_stride * 2, lsc = (uint32_t)tp.k.lc_stride * 2;   // code row bytes
     // this quarter's channel regions
     const uint32_t s_tv = smem_u32(smem + tp.off_tv) + (uint32_t)(chv * BTV) * boxb;
-    const uint32_t s_lv = smem_u32(smem + tp.off_lv) + (uint32_t)(chv * bcv) * boxb;
+    const uint32_t s_lv = smem_u32(smem + tp.off_lv) + (uint32_t)(chv * tp.lreg_v);
     const uint32_t s_tc = smem_u32(smem + tp.off_tc) + (uint32_t)(chc * BTC) * boxb;
-    const uint32_t s_lc = smem_u32(smem + tp.off_lc) + (uint32_t)(chc * bcc) * boxb;
+    const uint32_t s_lc = smem_u32(smem + tp.off_lc) + (uint32_t)(chc * tp.lreg_c);
     const bool io = slot == 0 && lane == 0;         // this channel's loading / storing thread
     // the item's old texels and last-transmitted codes of this quarter's channel
     auto issue_prefetch = [&](int item, bool vis) {
       const BlendVol& bv = a.v[vol_of(a, item)];
       const int p0 = (item - bv.item0) * np;
       if (vis) {
-        mbar_expect_tx(&efull[0], (uint32_t)((BTV + bcv) * np * 128));
+        mbar_expect_tx(&efull[0], (uint32_t)(BTV * np * 128) + (uint32_t)np * lsv);
         for (int b = 0; b < BTV; ++b) tma_load_3d(s_tv + (uint32_t)b * boxb, &bv.st_v, b * (128 / SB), p0, chv, &efull[0]);
-        for (int b = 0; b < bcv; ++b) tma_load_3d(s_lv + (uint32_t)b * boxb, &bv.last_v, b * 64, p0, chv, &efull[0]);
+        tma_load_3d(s_lv, &bv.last_v, 0, p0, chv, &efull[0]);
       } else {
-        mbar_expect_tx(&efull[1], (uint32_t)((BTC + bcc) * np * 128));
+        mbar_expect_tx(&efull[1], (uint32_t)(BTC * np * 128) + (uint32_t)np * lsc);
         for (int b = 0; b < BTC; ++b) tma_load_3d(s_tc + (uint32_t)b * boxb, &bv.st_c, b * (128 / SB), p0, chc, &efull[1]);
-        for (int b = 0; b < bcc; ++b) tma_load_3d(s_lc + (uint32_t)b * boxb, &bv.last_c, b * 64, p0, chc, &efull[1]);
+        tma_load_3d(s_lc, &bv.last_c, 0, p0, chc, &efull[1]);
       }
     };
     if (io) {
@@ -877,7 +957,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         bool chg = false;
         if (ok) {
           const uint32_t tm0 = tmem + ((uint32_t)(32 * q) << 16);
-          chg = epi_rows<NV, SB, 0, true>(on, slot, tm0, 0u, box_row(s_tv, boxb, jr), box_row(s_lv, boxb, jr),
+          chg = epi_rows<NV, SB, 0, true>(on, slot, tm0, 0u, box_row(s_tv, boxb, jr), s_lv + (uint32_t)jr * lsv,
                                           smem_u32(cf_v + chv * NV * S::RPV), smem_u32(km_v), h);
         }
         tc_fence_before();
@@ -895,8 +975,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         if (io) {
           if (ok) {
             for (int b = 0; b < BTV; ++b) tma_store_3d(&bv.st_v, b * (128 / SB), p0, chv, s_tv + (uint32_t)b * boxb);
-            if (kv.cur_v)
-              for (int b = 0; b < bcv; ++b) tma_store_3d(&bv.cur_v, b * 64, p0, chv, s_lv + (uint32_t)b * boxb);
+            if (kv.cur_v) tma_store_3d(&bv.cur_v, 0, p0, chv, s_lv);
             bulk_commit();
           }
           bulk_wait_read();                         // the boxes may be refilled now
@@ -911,7 +990,8 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         bool chg = false;
         if (ok) {
           const uint32_t tm0 = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)S::CBASE;
-          const BoxRow tb = box_row(s_tc, boxb, jr), cb = box_row(s_lc, boxb, jr);
+          const BoxRow tb = box_row(s_tc, boxb, jr);
+          const uint32_t cb = s_lc + (uint32_t)jr * lsc;
           const uint32_t tsplit = kSplitW ? (uint32_t)S::NCP : 0u;   // colour: hi and lo weight columns
           if (kind == PV_CODE_UNORM10)
             chg = epi_rows<NC, SB, PV_CODE_UNORM10, false>(on, slot, tm0, tsplit, tb, cb, smem_u32(cf_c), smem_u32(km_c), h);
@@ -933,8 +1013,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         if (io) {
           if (ok) {
             for (int b = 0; b < BTC; ++b) tma_store_3d(&bv.st_c, b * (128 / SB), p0, chc, s_tc + (uint32_t)b * boxb);
-            if (kv.cur_c)
-              for (int b = 0; b < bcc; ++b) tma_store_3d(&bv.cur_c, b * 64, p0, chc, s_lc + (uint32_t)b * boxb);
+            if (kv.cur_c) tma_store_3d(&bv.cur_c, 0, p0, chc, s_lc);
             bulk_commit();
           }
           bulk_wait_read();
@@ -1035,57 +1114,65 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int smem_max, Tc
   if (k.w_rb != ROWB || k.w_vb != Shp::NVP || k.w_rows != Shp::NVP + Shp::NCP) return cudaErrorInvalidValue;
   tp.k = k;
   tp.kc = k.w_kc;
-  // stage: the A (ray) tile [and its lo tile], then the weight plane(s)
-  size_t off = 0;
-  tp.off_x = 0;
-  off += A_BYTES;
-  tp.off_xlo = (int)off;
-  if (form != kF32) off += A_BYTES;
-  const size_t wb = (size_t)Shp::WROWS * ROWB;
-  tp.off_w = (int)off;
-  off += align1k(wb);
-  tp.off_wlo = (int)off;
-  if (form != kF16) off += align1k(wb);
-  tp.stage_bytes = (int)align1k(off);
   const int planes = form == kF16 ? 1 : 2;
-  // epilogue boxes: 128-byte column strips of np probe rows, each 1024-byte
-  // aligned (SWIZZLE_128B); tiles take (n+2)^2 * sb / 128 of them per probe
-  // row, codes one per 64 codes
+  // ray stage: the 128-row A tile (TMA rows at the lane quarters), plus for
+  // the 16-bit forms the lo A tile's first 64 rows (its other rows overlap
+  // what follows, lanes nothing reads); weight stage: the visibility block
+  // (the larger one) in every plane
+  tp.xstage = form != kF32 ? A_BYTES + A_BYTES / 2 : A_BYTES;
+  tp.wstage = (int)align1k((size_t)planes * Shp::WROWS * ROWB);
+  // epilogue: tile boxes (128-byte column strips of np rows, 1024-byte
+  // aligned for SWIZZLE_128B) and dense code rows per channel
   const int btv = (kNV + 2) * (kNV + 2) * sb / 128, btc = (kNC + 2) * (kNC + 2) * sb / 128;
-  const int bcv = (k.lv_stride + 63) / 64, bcc = (k.lc_stride + 63) / 64;
-  const int nbox = 2 * (btv + bcv) + 3 * (btc + bcc);
   const size_t tables = align1k((size_t)(2 * kNV * Shp::RPV + kNC * Shp::RPC) * 4) + align1k((size_t)(kNV + kNC) * 4);
   const size_t bars = 1024;
-  int np = np_want, stages = 0;
-  size_t epi = 0;
+  int np = np_want;
+  size_t epi = 0, rings = 0;
   for (; np >= 1; --np) {
-    epi = (size_t)nbox * align1k((size_t)np * 128);
+    tp.boxb = (int)align1k((size_t)np * 128);
+    tp.lreg_v = (int)align1k((size_t)np * k.lv_stride * 2);
+    tp.lreg_c = (int)align1k((size_t)np * k.lc_stride * 2);
+    epi = (size_t)(2 * btv + 3 * btc) * tp.boxb + 2 * (size_t)tp.lreg_v + 3 * (size_t)tp.lreg_c;
     const size_t need = 1024 + epi + tables + bars;
-    stages = need < (size_t)smem_max ? (int)(((size_t)smem_max - need) / tp.stage_bytes) : 0;
-    if (stages >= 3 || (np <= 8 && stages >= 2)) break;
+    rings = need < (size_t)smem_max ? (size_t)smem_max - need : 0;
+    if (rings >= (size_t)(3 * tp.xstage + 2 * tp.wstage)) break;
   }
-  if (np < 1 || stages < 2) return cudaErrorInvalidConfiguration;
-  if (stages > kMaxStages) stages = kMaxStages;
-  // F32: the A ring lives in TMEM after the accumulators, 32 columns per stage
+  if (np < 1) return cudaErrorInvalidConfiguration;
+  // The weight tiles come from L2 and need a shallow ring (3 stages of the
+  // split forms' 26 KB, 4 of 13 KB); the ray tiles come from HBM, so the ray
+  // ring takes the rest (up to 16 stages) to keep enough bytes in flight.
+  int ws = tp.wstage > 16384 ? 3 : 4;
+  while (ws > 2 && (size_t)ws * tp.wstage + (size_t)3 * tp.xstage > rings) --ws;
+  int xs = (int)((rings - (size_t)ws * tp.wstage) / tp.xstage);
+  if (xs > 16) xs = 16;
+  if (xs < 2) return cudaErrorInvalidConfiguration;
   tp.abase = round_up_c(Shp::CBASE + 2 * Shp::NCP, 32);
-  if (form == kF32 && tp.abase + 32 * stages > 512) stages = (512 - tp.abase) / 32;
+  tp.as_ = form == kF32 ? (512 - tp.abase) / 32 : 1;
+  if (tp.as_ > 6) tp.as_ = 6;
+  if (form == kF32 && tp.as_ < 2) return cudaErrorInvalidConfiguration;
   tp.np = np;
-  tp.stages = stages;
-  tp.tx_v = (uint32_t)(np * ROWB) + (uint32_t)(planes * Shp::NVP * ROWB);
-  tp.tx_c = (uint32_t)(3 * np * ROWB) + (uint32_t)(planes * Shp::NCP * ROWB);
+  tp.xs = xs;
+  tp.ws = ws;
+  tp.tx_xv = (uint32_t)(np * ROWB);
+  tp.tx_xc = (uint32_t)(3 * np * ROWB);
+  tp.tx_wv = (uint32_t)(planes * Shp::NVP * ROWB);
+  tp.tx_wc = (uint32_t)(planes * Shp::NCP * ROWB);
   tp.idesc_v = make_idesc(form, 128, Shp::NVP);
   tp.idesc_c = make_idesc(form, 128, Shp::NCP);
   tp.idesc_c2 = make_idesc(form, 128, 2 * Shp::NCP);
-  tp.boxb = (int)align1k((size_t)np * 128);
-  off = (size_t)stages * tp.stage_bytes;
+  size_t off = 0;
+  tp.off_xr = (int)off;
+  off += (size_t)xs * tp.xstage;
+  tp.off_wr = (int)off;
+  off += (size_t)ws * tp.wstage;
   tp.off_tv = (int)off;
   off += (size_t)2 * btv * tp.boxb;
   tp.off_lv = (int)off;
-  off += (size_t)2 * bcv * tp.boxb;
+  off += (size_t)2 * tp.lreg_v;
   tp.off_tc = (int)off;
   off += (size_t)3 * btc * tp.boxb;
   tp.off_lc = (int)off;
-  off += (size_t)3 * bcc * tp.boxb;
+  off += (size_t)3 * tp.lreg_c;
   tp.off_cf = (int)off;
   off += align1k((size_t)(2 * kNV * Shp::RPV + kNC * Shp::RPC) * 4);
   tp.off_km = (int)off;
@@ -1096,18 +1183,19 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int smem_max, Tc
   return (*smem <= (size_t)smem_max) ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
-// [channels][rows][inner] elements of esize bytes, boxes of 128 bytes x
-// box_rows x 1 with SWIZZLE_128B; out-of-range rows and columns read zero
+// [channels][rows][inner] elements of esize bytes. Tiles (dense = false):
+// boxes of 128 bytes x box_rows x 1 with SWIZZLE_128B; codes (dense = true):
+// boxes of whole rows x box_rows x 1, unswizzled. Out-of-range rows read zero
 // and are not written.
 cudaError_t encode_3d(CUtensorMap* m, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner,
-                      uint64_t rows, uint64_t nch, uint32_t box_rows) {
+                      uint64_t rows, uint64_t nch, uint32_t box_rows, bool dense) {
   cuuint64_t dims[3] = {inner, rows, nch};
   cuuint64_t strides[2] = {inner * esize, rows * inner * esize};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / esize), box_rows, 1};
+  cuuint32_t box[3] = {dense ? (cuuint32_t)inner : (cuuint32_t)(128 / esize), box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = g_encode(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        dense ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -1116,12 +1204,12 @@ cudaError_t encode_epi_maps(const pv_dev& k, int np, BlendVol& bv) {
   const int sb = k.state_fmt == PV_FMT_F16 ? 2 : 4;
   const CUtensorMapDataType st = sb == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
   const CUtensorMapDataType cd = CU_TENSOR_MAP_DATA_TYPE_UINT16;
-  cudaError_t e = encode_3d(&bv.st_v, st, sb, k.state_v, k.sv_stride, k.P, 2, np);
-  if (e == cudaSuccess) e = encode_3d(&bv.st_c, st, sb, k.state_c, k.sc_stride, k.P, 3, np);
-  if (e == cudaSuccess) e = encode_3d(&bv.last_v, cd, 2, k.last_v, k.lv_stride, k.P, 2, np);
-  if (e == cudaSuccess) e = encode_3d(&bv.last_c, cd, 2, k.last_c, k.lc_stride, k.P, 3, np);
-  if (e == cudaSuccess && k.cur_v) e = encode_3d(&bv.cur_v, cd, 2, k.cur_v, k.lv_stride, k.P, 2, np);
-  if (e == cudaSuccess && k.cur_c) e = encode_3d(&bv.cur_c, cd, 2, k.cur_c, k.lc_stride, k.P, 3, np);
+  cudaError_t e = encode_3d(&bv.st_v, st, sb, k.state_v, k.sv_stride, k.P, 2, np, false);
+  if (e == cudaSuccess) e = encode_3d(&bv.st_c, st, sb, k.state_c, k.sc_stride, k.P, 3, np, false);
+  if (e == cudaSuccess) e = encode_3d(&bv.last_v, cd, 2, k.last_v, k.lv_stride, k.P, 2, np, true);
+  if (e == cudaSuccess) e = encode_3d(&bv.last_c, cd, 2, k.last_c, k.lc_stride, k.P, 3, np, true);
+  if (e == cudaSuccess && k.cur_v) e = encode_3d(&bv.cur_v, cd, 2, k.cur_v, k.lv_stride, k.P, 2, np, true);
+  if (e == cudaSuccess && k.cur_c) e = encode_3d(&bv.cur_c, cd, 2, k.cur_c, k.lc_stride, k.P, 3, np, true);
   return e;
 }
 
