@@ -84,6 +84,12 @@ constexpr int ROWB = 64;                 // bytes per K-chunk row (SWIZZLE_64B):
 constexpr int QROWS = 32;                // probe rows per lane quarter
 constexpr int A_BYTES = 128 * ROWB;      // one 128-row A tile of a stage
 constexpr int EPI_THREADS = 256;         // warps 8..15
+// exchange of the visibility accumulators' second parts between lane
+// quarters: per lane two interior rows of up to 16 texels (4-byte floats,
+// a row of 8 16-byte units: distinct bank groups for 8 consecutive lanes),
+// two buffers per warp pair
+constexpr uint32_t XROW_BYTES = 2 * 14 * 4;
+constexpr uint32_t XBUF_BYTES = 32 * XROW_BYTES;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 // binary16 operand form: d^2 enters the MMA scaled by 2^-4 (exact), which
 // keeps the high part of d^2 for hit distances up to 2^10 in binary16 range
@@ -110,7 +116,7 @@ struct TcParams {
   int off_tv, off_lv, off_tc, off_lc;    // epilogue regions: visibility tiles / codes, colour tiles / codes
   int boxb;                              // bytes reserved per tile box (np rows of 128 bytes, 1024-aligned)
   int lreg_v, lreg_c;                    // bytes reserved per channel of code rows (np dense rows)
-  int off_cf, off_km, off_bar;           // tables, barriers
+  int off_cf, off_km, off_xb, off_bar;   // tables, exchange buffers, barriers
   uint32_t tx_xv, tx_xc, tx_wv, tx_wc;   // bytes per ray / weight stage, visibility / colour phase
   uint32_t idesc_v, idesc_c, idesc_c2;   // instruction descriptors (N = NVP, NCP, 2 NCP)
   int abase;                             // F32: first TMEM column of the A ring (32 columns per stage)
@@ -209,6 +215,17 @@ __device__ __forceinline__ void fence_proxy_async() {
 }
 __device__ __forceinline__ void named_bar(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+// Named barrier that also returns the AND of every participant's flag, so
+// that the threads meeting there take the same branch afterwards.
+__device__ __forceinline__ bool named_bar_and(int id, int threads, bool flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.b32 a, %1, 0;\n bar.red.and.pred b, %2, %3, a;\n selp.u32 %0, 1, 0, b;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)flag), "r"(id), "r"(threads)
+      : "memory");
+  return r != 0;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -458,8 +475,12 @@ __device__ __forceinline__ void store_row(bool on, const BoxRow& tb, int ti, uin
 // diagonally opposite interior corners. Writes the tile rows and the codes,
 // and returns whether any code differs from the last transmitted one.
 template <int N, int SB, int KIND, bool VIS>
+//   xb      != 0: the rows' second parts come from the partner warp through
+//           this exchange buffer (lane-major, rows i then N-1-i), after the
+//           rendezvous at named barrier xbar
 __device__ __forceinline__ bool update_pair(bool on, int i, uint32_t tm0, uint32_t tsplit, const BoxRow& tb,
-                                            uint32_t cb, uint32_t s_cf, uint32_t s_km, float h) {
+                                            uint32_t cb, uint32_t s_cf, uint32_t s_km, float h, uint32_t xb,
+                                            int xbar) {
   constexpr int RP = round_up_c(N, 4);
   const int i2 = N - 1 - i;
   const uint32_t qa = 2u * N * i, qb = 2u * N * i2;  // code row offsets of the two rows
@@ -474,7 +495,21 @@ __device__ __forceinline__ bool update_pair(bool on, int i, uint32_t tm0, uint32
     lb[m] = lds32(cb + qb + 4u * m);
   }
   const uint32_t kma = lds32(s_km + 4u * i), kmb = lds32(s_km + 4u * i2);
+  if (xb) named_bar(xbar, 64);                       // the partner wrote this pair's second parts
   tmem_wait_ld();
+  if (xb) {
+#pragma unroll
+    for (int c = 0; c < N / 2; ++c) {
+      float v[4];
+      lds128f(xb + 16u * c, v[0], v[1], v[2], v[3]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int t = 4 * c + e;
+        if (t < N) ra.acc[t] += v[e];
+        else if (t < 2 * N) rb.acc[t - N] += v[e];
+      }
+    }
+  }
   uint32_t a[N], b[N], ca[N / 2], cc[N / 2];
   finish_row<N, SB, KIND, VIS>(ra, tsplit != 0, s_cf + 4u * RP * i, kma, h, a, ca);
   finish_row<N, SB, KIND, VIS>(rb, tsplit != 0, s_cf + 4u * RP * i2, kmb, h, b, cc);
@@ -507,11 +542,43 @@ __device__ __forceinline__ bool update_pair(bool on, int i, uint32_t tm0, uint32
 // its slot (p % 2 == slot). Returns whether any code of the row changed.
 template <int N, int SB, int KIND, bool VIS>
 __device__ __forceinline__ bool epi_rows(bool on, int slot, uint32_t tm0, uint32_t tsplit, const BoxRow& tb,
-                                         uint32_t cb, uint32_t s_cf, uint32_t s_km, float h) {
+                                         uint32_t cb, uint32_t s_cf, uint32_t s_km, float h, uint32_t xbuf,
+                                         int xbar, int lane) {
   bool ch = false;
+  int k = 0;
 #pragma unroll 1
-  for (int p = slot; p < N / 2; p += 2) ch |= update_pair<N, SB, KIND, VIS>(on, p, tm0, tsplit, tb, cb, s_cf, s_km, h);
+  for (int p = slot; p < N / 2; p += 2, ++k) {
+    const uint32_t xb = xbuf ? xbuf + (uint32_t)(k & 1) * XBUF_BYTES + (uint32_t)lane * XROW_BYTES : 0u;
+    ch |= update_pair<N, SB, KIND, VIS>(on, p, tm0, tsplit, tb, cb, s_cf, s_km, h, xb, xbar);
+  }
   return ch;
+}
+
+// The partner side of the exchange: this warp's lanes hold the second parts
+// of the partner warp's rows (the same probes, lo halves of the operands);
+// per row pair it moves them from TMEM into the exchange buffer (double
+// buffered by pair parity) and meets the partner at named barrier xbar.
+template <int N>
+__device__ __forceinline__ void provide_rows(int slot, uint32_t tm0, uint32_t xbuf, int xbar, int lane) {
+  int k = 0;
+#pragma unroll 1
+  for (int p = slot; p < N / 2; p += 2, ++k) {
+    const int i = p, i2 = N - 1 - p;
+    float v[2 * N + 2];
+#pragma unroll
+    for (int m = 0; m < N / 2; ++m) {
+      tmem_ld2(tm0 + (uint32_t)(N * i) + 2u * m, v[2 * m], v[2 * m + 1]);
+      tmem_ld2(tm0 + (uint32_t)(N * i2) + 2u * m, v[N + 2 * m], v[N + 2 * m + 1]);
+    }
+    tmem_wait_ld();
+    const uint32_t xb = xbuf + (uint32_t)(k & 1) * XBUF_BYTES + (uint32_t)lane * XROW_BYTES;
+#pragma unroll
+    for (int c = 0; c < N / 2; ++c)
+      asm volatile("st.shared.v4.f32 [%0], {%1,%2,%3,%4};" ::"r"(xb + 16u * c), "f"(v[4 * c]), "f"(v[4 * c + 1]),
+                   "f"(v[4 * c + 2]), "f"(v[4 * c + 3])
+                   : "memory");
+    named_bar(xbar, 64);
+  }
 }
 
 // ------------------------------------------------------------------ kernel
@@ -525,7 +592,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool kSplitW = FORM != kF16;
   constexpr bool kTmemA = FORM == kF32;
-  constexpr bool kD2Lo = FORM != kF32;               // 16-bit forms: d^2 as hi + lo
+  static_assert(2 * NV * 4 <= (int)XROW_BYTES, "exchange rows hold two visibility interior rows");
   constexpr uint32_t TBV = (uint32_t)((NV + 2) * (NV + 2) * SB), TBC = (uint32_t)((NC + 2) * (NC + 2) * SB);
   constexpr uint32_t WLO_V = (uint32_t)S::NVP * ROWB;              // visibility lo plane offset in a weight stage
 
@@ -556,7 +623,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
       mbar_init(&aempty[i], 1);
     }
     for (int b = 0; b < 2; ++b) mbar_init(&tfull[b], 1);
-    mbar_init(&tempty[0], 4);                        // visibility epilogue warps (quarters 0, 1)
+    mbar_init(&tempty[0], kTmemA ? 8 : 6);           // visibility epilogue warps and their partners
     mbar_init(&tempty[1], 6);                        // colour epilogue warps (quarters 1, 2, 3)
     mbar_init(&efull[0], 2);                         // one loading thread per visibility channel
     mbar_init(&efull[1], 3);                         // and per colour channel
@@ -693,22 +760,21 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
               const uint64_t bw = sdesc(wb + kb);
               if constexpr (kTmemA) {
                 const uint32_t ah = tmem + (uint32_t)tp.abase + 32u * sa + 8u * ks;
-                if (phase == 0) {
-                  mma_ts_tf32(d, ah, bw, idesc, acc);                          // hi * hi
-                  mma_ts_tf32(d, ah, sdesc(wb + WLO_V + kb), idesc, 1u);       // hi * lo
+                if (phase == 0) {                                              // lanes hold hi and lo parts
+                  mma_ts_tf32(d, ah, bw, idesc, acc);                          // [d, d^2] (hi | lo) * W hi
+                  mma_ts_tf32(d, ah, sdesc(wb + WLO_V + kb), idesc, 1u);       // ... * W lo
                 } else {
-                  mma_ts_tf32(d, ah, bw, tp.idesc_c2, acc);                    // hi * [hi | lo]
+                  mma_ts_tf32(d, ah, bw, tp.idesc_c2, acc);                    // x hi * [W hi | W lo]
+                  mma_ts_tf32(d, ah + 16u, bw, idesc, 1u);                     // x lo * W hi
                 }
-                mma_ts_tf32(d, ah + 16u, bw, idesc, 1u);                       // lo * hi
               } else {
                 const uint64_t ax = sdesc(xa + kb);
                 if (kSplitW && phase == 1) {
-                  mma_ss<FORM>(d, ax, bw, tp.idesc_c2, acc);                   // x * [hi | lo]
+                  mma_ss<FORM>(d, ax, bw, tp.idesc_c2, acc);                   // x * [W hi | W lo]
                 } else {
-                  mma_ss<FORM>(d, ax, bw, idesc, acc);
+                  mma_ss<FORM>(d, ax, bw, idesc, acc);                         // visibility: d, d^2 hi, d^2 lo
                   if (kSplitW) mma_ss<FORM>(d, ax, sdesc(wb + WLO_V + kb), idesc, 1u);
                 }
-                if (kD2Lo && phase == 0) mma_ss<FORM>(d, sdesc(xa + A_BYTES + kb), bw, idesc, 1u);   // d^2 lo
               }
             }
             // stages free once these MMAs finish
@@ -737,14 +803,6 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   } else if (warp >= 4 && warp < 8) {
     // ------------------------------------------------------------ converters
     const int q = warp & 3;
-    if constexpr (kD2Lo) {
-      // the lo A tile's visibility d lanes stay zero: its MMA adds d^2 lo only
-      if (q == 0)
-        for (int s = 0; s < tp.xs; ++s)
-          for (int o = lane * 16; o < QROWS * ROWB; o += 32 * 16)
-            *(uint4*)(xring + (size_t)s * tp.xstage + A_BYTES + o) = make_uint4(0u, 0u, 0u, 0u);
-      fence_proxy_async();
-    }
     int x = 0, sa = 0;
     uint32_t ph = 0, aph = 0;
     bool ok = true;
@@ -765,14 +823,18 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
           if (!ok) break;
           const uint32_t sx = smem_u32(xring + (size_t)x * tp.xstage);
           if constexpr (kTmemA) {
-            // my lane quarter's rows: visibility q0 = d, q1 = d^2 (from d);
-            // colour q1..q3 = R, G, B; each split into TF32 hi + lo in TMEM
+            // my lane quarter's rows, split into TF32 hi + lo parts in TMEM.
+            // Visibility: q0 = d hi, q1 = d^2 hi, q2 = d lo, q3 = d^2 lo (all
+            // from the d rows), in the stage's first 16 columns, so that each
+            // MMA takes both parts and the epilogue adds quarter 2 to 0 and 3
+            // to 1. Colour: q1..q3 = R, G, B, hi in the first 16 columns and
+            // lo in the next 16.
             ok = mbar_wait(&aempty[sa], aph ^ 1, err);
             if (!ok) break;
             tc_fence_after();
-            const bool work = phase == 0 ? q <= 1 : q >= 1;
-            if (work) {
+            if (phase == 0 || q >= 1) {
               const int row = phase == 0 ? lane : 32 * q + lane;
+              const bool sq = phase == 0 && (q & 1);
               uint32_t hi[16], lo[16];
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
@@ -782,7 +844,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                   float v = __uint_as_float(xs[e]);
-                  if (phase == 0 && q == 1) v = v * v;
+                  if (sq) v = v * v;
                   const uint32_t vb = __float_as_uint(v);
                   const uint32_t h = vb & 0xFFFFE000u;
                   hi[4 * u + e] = h;
@@ -790,8 +852,12 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
                 }
               }
               const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)tp.abase + 32u * sa;
-              tmem_st16(ta, hi);
-              tmem_st16(ta + 16u, lo);
+              if (phase == 0) {
+                tmem_st16(ta, q < 2 ? hi : lo);
+              } else {
+                tmem_st16(ta, hi);
+                tmem_st16(ta + 16u, lo);
+              }
               tmem_wait_st();
             }
             tc_fence_before();
@@ -807,10 +873,10 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
           } else {
             // d^2 = hi + lo in the operand format (binary16 scaled by 2^-4):
             // the hi part into lane quarter 1 of the A tile, the lo part into
-            // lane quarter 1 of the lo A tile; converter warp q takes 16-byte
-            // unit q of every d row (8 rays), so the four share each chunk
+            // lane quarter 2 (the epilogue adds quarter 2's accumulators to
+            // quarter 1's); converter warp q takes 16-byte unit q of every d
+            // row (8 rays), so the four share each chunk
             if (phase == 0) {
-              const uint32_t sxl = sx + A_BYTES;
               const int u = q;
               uint32_t r[4];
               lds128(sx + swz64(lane, u), r[0], r[1], r[2], r[3]);
@@ -837,14 +903,12 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
                   ol[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
                 }
               }
-              const uint32_t o = swz64(QROWS + lane, u);
-              asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + o), "r"(oh[0]), "r"(oh[1]), "r"(oh[2]),
-                           "r"(oh[3])
+              asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + swz64(QROWS + lane, u)), "r"(oh[0]),
+                           "r"(oh[1]), "r"(oh[2]), "r"(oh[3])
                            : "memory");
-              if (kD2Lo)
-                asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sxl + o), "r"(ol[0]), "r"(ol[1]),
-                             "r"(ol[2]), "r"(ol[3])
-                             : "memory");
+              asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + swz64(2 * QROWS + lane, u)), "r"(ol[0]),
+                           "r"(ol[1]), "r"(ol[2]), "r"(ol[3])
+                           : "memory");
               fence_proxy_async();
             }
             __syncwarp();
@@ -879,6 +943,15 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     const uint32_t s_tc = smem_u32(smem + tp.off_tc) + (uint32_t)(chc * BTC) * boxb;
     const uint32_t s_lc = smem_u32(smem + tp.off_lc) + (uint32_t)(chc * tp.lreg_c);
     const bool io = slot == 0 && lane == 0;         // this channel's loading / storing thread
+    // visibility exchange: F32 lanes of quarters 2 / 3 hold the lo parts of
+    // quarters 0 / 1 (d, d^2); 16-bit lanes of quarter 2 hold d^2's lo part
+    // (quarter 1). A target warp meets its provider (same slot) at its own
+    // named barrier and reads the provider's values from a double buffer.
+    const bool x_target = kTmemA ? q <= 1 : q == 1;
+    const bool x_provider = kTmemA ? q >= 2 : q == 2;
+    const int x_t = kTmemA ? (q & 1) : 0;           // partnership index of this quarter's target
+    const int xbar = 6 + 2 * x_t + slot;
+    const uint32_t xbuf = smem_u32(smem + tp.off_xb) + (uint32_t)((2 * x_t + slot) * 2) * XBUF_BYTES;
     // the item's old texels and last-transmitted codes of this quarter's channel
     auto issue_prefetch = [&](int item, bool vis) {
       const BlendVol& bv = a.v[vol_of(a, item)];
@@ -950,15 +1023,26 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
       }
       const int next = item + gridDim.x;
       // ---- visibility
+      if (x_provider) {                             // the lo parts of a partner quarter's rows
+        if (ok) ok = mbar_wait(&tfull[0], eph, err);
+        tc_fence_after();
+        ok = named_bar_and(xbar, 64, ok);
+        if (ok) provide_rows<NV>(slot, tmem + ((uint32_t)(32 * q) << 16), xbuf, xbar, lane);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[0]);
+      }
       if (do_v) {
         if (ok) ok = mbar_wait(&efull[0], eph, err);
         if (ok) ok = mbar_wait(&tfull[0], eph, err);
         tc_fence_after();
+        if (x_target) ok = named_bar_and(xbar, 64, ok);
         bool chg = false;
         if (ok) {
           const uint32_t tm0 = tmem + ((uint32_t)(32 * q) << 16);
           chg = epi_rows<NV, SB, 0, true>(on, slot, tm0, 0u, box_row(s_tv, boxb, jr), s_lv + (uint32_t)jr * lsv,
-                                          smem_u32(cf_v + chv * NV * S::RPV), smem_u32(km_v), h);
+                                          smem_u32(cf_v + chv * NV * S::RPV), smem_u32(km_v), h,
+                                          x_target ? xbuf : 0u, xbar, lane);
         }
         tc_fence_before();
         __syncwarp();
@@ -994,9 +1078,11 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
           const uint32_t cb = s_lc + (uint32_t)jr * lsc;
           const uint32_t tsplit = kSplitW ? (uint32_t)S::NCP : 0u;   // colour: hi and lo weight columns
           if (kind == PV_CODE_UNORM10)
-            chg = epi_rows<NC, SB, PV_CODE_UNORM10, false>(on, slot, tm0, tsplit, tb, cb, smem_u32(cf_c), smem_u32(km_c), h);
+            chg = epi_rows<NC, SB, PV_CODE_UNORM10, false>(on, slot, tm0, tsplit, tb, cb, smem_u32(cf_c),
+                                                           smem_u32(km_c), h, 0u, 0, lane);
           else
-            chg = epi_rows<NC, SB, PV_CODE_UF10, false>(on, slot, tm0, tsplit, tb, cb, smem_u32(cf_c), smem_u32(km_c), h);
+            chg = epi_rows<NC, SB, PV_CODE_UF10, false>(on, slot, tm0, tsplit, tb, cb, smem_u32(cf_c), smem_u32(km_c),
+                                                        h, 0u, 0, lane);
         }
         tc_fence_before();
         __syncwarp();
@@ -1115,16 +1201,16 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int smem_max, Tc
   tp.k = k;
   tp.kc = k.w_kc;
   const int planes = form == kF16 ? 1 : 2;
-  // ray stage: the 128-row A tile (TMA rows at the lane quarters), plus for
-  // the 16-bit forms the lo A tile's first 64 rows (its other rows overlap
-  // what follows, lanes nothing reads); weight stage: the visibility block
-  // (the larger one) in every plane
-  tp.xstage = form != kF32 ? A_BYTES + A_BYTES / 2 : A_BYTES;
+  // ray stage: the 128-row A tile (TMA rows at the lane quarters); weight
+  // stage: the visibility block (the larger one) in every plane
+  tp.xstage = A_BYTES;
   tp.wstage = (int)align1k((size_t)planes * Shp::WROWS * ROWB);
   // epilogue: tile boxes (128-byte column strips of np rows, 1024-byte
   // aligned for SWIZZLE_128B) and dense code rows per channel
   const int btv = (kNV + 2) * (kNV + 2) * sb / 128, btc = (kNC + 2) * (kNC + 2) * sb / 128;
-  const size_t tables = align1k((size_t)(2 * kNV * Shp::RPV + kNC * Shp::RPC) * 4) + align1k((size_t)(kNV + kNC) * 4);
+  const size_t xbytes = (size_t)(form == kF32 ? 4 : 2) * 2 * XBUF_BYTES;   // visibility exchange buffers
+  const size_t tables = align1k((size_t)(2 * kNV * Shp::RPV + kNC * Shp::RPC) * 4) + align1k((size_t)(kNV + kNC) * 4) +
+                        align1k(xbytes);
   const size_t bars = 1024;
   int np = np_want;
   size_t epi = 0, rings = 0;
@@ -1177,6 +1263,8 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int smem_max, Tc
   off += align1k((size_t)(2 * kNV * Shp::RPV + kNC * Shp::RPC) * 4);
   tp.off_km = (int)off;
   off += align1k((size_t)(kNV + kNC) * 4);
+  tp.off_xb = (int)off;
+  off += align1k(xbytes);
   tp.off_bar = (int)off;
   off += bars;
   *smem = off + 1024;                          // slack for aligning the dynamic base
