@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-client", action="store_true")
     ap.add_argument("--no-views", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=20.0)
+    ap.add_argument("--client-only", action="store_true",
+                    help="time only the client decode (L2 flushed before each launch) and print its object")
     return ap.parse_args()
 
 
@@ -270,9 +272,33 @@ def time_form(spec, steps, warmup, seed):
     blend = [events[s][1].elapsed_time(events[s][2]) for s in range(nb)]
     weights = [events[s][0].elapsed_time(events[s][1]) for s in range(nb)]
     pack = [events[s][2].elapsed_time(events[s][3]) for s in range(nb)]
+    # each kernel alone: a graph of KRUN back-to-back launches of it (consecutive frames of
+    # the cycled inputs), CUDA events around the whole replay on the launching stream; the
+    # average launch duration is what the roofline divides by
+    alone = {}
+    if use_graphs:
+        krun = 16
+        calls = {"weights": lambda s: pv.probe_update_weights(vol.handle, bufs[s % NBUF][2]),
+                 "blend": lambda s: pv.probe_update_blend(vol.handle, bufs[s % NBUF][0], bufs[s % NBUF][1]),
+                 "select_pack": lambda s: vol.select_and_pack()}
+        for name, call in calls.items():
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for s in range(krun):
+                    call(s)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                g.replay()
+                a, b = ev(), ev()
+                a.record(stream)
+                for _ in range(2):
+                    g.replay()
+                b.record(stream)
+            torch.cuda.synchronize()
+            alone[name] = a.elapsed_time(b) / (2 * krun)
     res = dict(total_ms=total_ms, blend_ms=statistics.mean(blend), weights_ms=statistics.mean(weights),
                select_pack_ms=statistics.mean(pack), kernel=vol.kernel, graphs=use_graphs,
-               launches_per_step=3)
+               launches_per_step=3, alone_ms=alone)
     vol.close()
     del bufs
     torch.cuda.empty_cache()
@@ -599,12 +625,94 @@ def time_views(seed, clients=4, frames=30, nbuf=8):
             "separate_volumes": {"value": clients * P / (ms_sep / 1e3), "ms_per_frame": ms_sep}}
 
 
-def time_served(seconds, seed):
+def _served_paced(arrivals, inputs, seconds, budget, slots, serial):
+    """The request loop on a 60 Hz wall clock: at each tick boundary (the loop sleeps until it)
+    the clients that have arrived by then are opened, those whose sessions ended are closed,
+    and every admitted client submits its rays; the server launches the tick's batch and the
+    loop polls each request. Per request: wall time from its submission to the poll that
+    returns its frame. Per tick: wall time from the first submission to the last completion.
+    serial: each request is a plain update + select/pack of the client's own volume."""
+    import torch
+    import paper_2103_05875_gb300 as pv
+    server = None if serial else pv.ProbeServer(budget, slots)
+    singles, active = {}, {}
+    pending = list(sorted(arrivals, key=lambda a: a.arrive_s))
+    waits, probes, req_lat, tick_lat, ticks_late = 0, 0, [], [], 0
+    t_start = time.perf_counter()
+    n_ticks = int(seconds * 60)
+    for t in range(n_ticks):
+        target = t_start + t / 60.0
+        now = time.perf_counter()
+        if now < target:
+            time.sleep(target - now)
+        else:
+            ticks_late += 1 if now - target > 1 / 60.0 else 0
+        wall = time.perf_counter() - t_start
+        while pending and pending[0].arrive_s <= wall:     # arrivals by wall time
+            a = pending.pop(0)
+            if serial:
+                singles[a.client] = pv.ProbeVolume(a.spec)
+            elif not server.open(a.client, a.spec):
+                waits += 1
+            active[a.client] = a
+        for c, a in list(active.items()):                   # sessions that ended
+            if wall > a.arrive_s + a.session_s:
+                if serial:
+                    singles.pop(c).close()
+                else:
+                    server.close(c)
+                del active[c]
+        t0 = time.perf_counter()
+        if serial:
+            subs = []
+            for c, a in active.items():
+                r, d, q = inputs[(a.spec.nx, a.spec.ny, a.spec.nz, a.spec.rays)][t % 2]
+                ts = time.perf_counter()
+                singles[c].update(r, d, q)
+                singles[c].select_and_pack()
+                subs.append((ts, a.spec.probes))
+            if subs:
+                torch.cuda.synchronize()
+                done = time.perf_counter()
+                req_lat += [(done - ts) * 1e3 for ts, _ in subs]
+                probes += sum(p for _, p in subs)
+        else:
+            reqs = []
+            for c, a in active.items():
+                if server.status(c)[0] != 1:
+                    continue
+                r, d, q = inputs[(a.spec.nx, a.spec.ny, a.spec.nz, a.spec.rays)][t % 2]
+                reqs.append((server.submit(c, r, d, q), time.perf_counter(), a.spec.probes))
+            if reqs:
+                server.tick()
+                left = list(reqs)
+                while left:
+                    still = []
+                    for tk, ts, pr in left:
+                        if server.poll(tk) is None:
+                            still.append((tk, ts, pr))
+                        else:
+                            req_lat.append((time.perf_counter() - ts) * 1e3)
+                            probes += pr
+                    left = still
+        if active:
+            tick_lat.append((time.perf_counter() - t0) * 1e3)
+    wall_s = time.perf_counter() - t_start
+    for v in singles.values():
+        v.close()
+    if server is not None:
+        server.close_server()
+    return probes, req_lat, tick_lat, waits, wall_s, ticks_late
+
+
+def time_served(seconds, seed, paced_seconds=8.0):
     """Served form: 64 clients arriving Poisson(4/s) with exponential sessions (mean 8 s), each
-    owning a volume of the batched workload's sizes; 60 Hz ticks over `seconds` of simulated
-    time, run back to back; per-tick latency from the first submission to the last completed
-    poll (through the public API, host loop included). Against the same schedule served by
-    plain per-client updates."""
+    owning a volume of the batched workload's sizes. Paced: the request loop on a 60 Hz wall
+    clock, arrivals by wall time, per-request latency from submission to the completing poll
+    (public API, host loop included). Throughput: probes served over the time the ticks took.
+    Back-to-back: the same schedule of `seconds` simulated time with the ticks run back to
+    back (device-bound throughput). Both against the same schedule served by plain per-client
+    updates."""
     import torch
     import pv_workload as wl
     arrivals = wl.served_clients(64, 4.0, 8.0, seed=seed)
@@ -624,15 +732,63 @@ def time_served(seconds, seed):
         return {"value": probes / total_s if total_s else 0.0, "unit": UNIT,
                 "p50_ms": q[len(q) // 2] if q else None, "p99_ms": q[min(len(q) - 1, int(0.99 * len(q)))] if q else None,
                 "ticks": len(lat), "client_updates_probes": probes, "admission_waits": waits}
+    def paced(serial, budget, slots):
+        probes, req, tick, waits, wall_s, late = _served_paced(arrivals, shapes, paced_seconds, budget, slots, serial)
+        q, tq = sorted(req), sorted(tick)
+        busy_s = sum(tick) / 1e3
+        pick = lambda v, f: v[min(len(v) - 1, int(f * len(v)))] if v else None  # noqa: E731
+        return {"paced": True, "seconds": round(wall_s, 2), "requests": len(req),
+                "request_latency_ms": {"p50": pick(q, 0.5), "p99": pick(q, 0.99), "max": q[-1] if q else None},
+                "tick_ms": {"p50": pick(tq, 0.5), "p99": pick(tq, 0.99)},
+                "value": probes / busy_s if busy_s else 0.0, "unit": UNIT,
+                "offered_probes_per_s": probes / wall_s, "admission_waits": waits, "ticks_late": late}
     res = {"workload": f"64 clients, Poisson 4/s arrivals, exp(8 s) sessions, batched-workload sizes, "
-                       f"60 Hz ticks, {seconds:g} s simulated, 40 GB budget"}
-    res.update(summarise(*_served_run(arrivals, shapes, ticks, 40 << 30, 64, serial=False)))
-    res["serial_plain"] = summarise(*_served_run(arrivals, shapes, ticks, 40 << 30, 64, serial=True))
-    tight = summarise(*_served_run(arrivals, shapes, ticks, 256 << 20, 16, serial=False))
-    res["tight_budget_256MB_16_slots"] = tight
+                       f"60 Hz ticks, 40 GB budget"}
+    res.update(paced(False, 40 << 30, 64))
+    res["serial_plain"] = paced(True, 40 << 30, 64)
+    res["tight_budget_256MB_16_slots"] = paced(False, 256 << 20, 16)
+    bb = summarise(*_served_run(arrivals, shapes, ticks, 40 << 30, 64, serial=False))
+    bb["serial_plain"] = summarise(*_served_run(arrivals, shapes, ticks, 40 << 30, 64, serial=True))
+    res["back_to_back"] = dict(bb, note=f"{seconds:g} s of simulated ticks run without pacing")
     del shapes
     torch.cuda.empty_cache()
     return res
+
+
+def accuracy_report(seed, forms=("f32", "f16", "bf16")):
+    """Per-texel relative error of the blended mean against the FP64 oracle, per operand form:
+    16^3 probes x 256 rays, hysteresis 0 and FP32 state (the stored texel is the frame mean),
+    one frame. relative error = |got - ref| / max(|ref|, 1e-6 max|ref|)."""
+    import numpy as np
+    import torch
+    import paper_2103_05875_gb300 as pv
+    import pv_workload as wl
+    from oracle import blend, octahedral
+    out = {}
+    for form in forms:
+        spec = wl.VolumeSpec(16, 16, 16, 256, hysteresis=0.0, state_fmt="f32", operand_fmt=form)
+        fs = wl.FrameStream(spec, seed)
+        rad = wl.to_operand(fs.radiance(0), form)
+        dist = wl.to_operand(fs.dist(0), form)
+        dirs = torch.from_numpy(fs.directions(0))
+        vol = pv.ProbeVolume(spec)
+        vol.update(rad.cuda(), dist.cuda(), dirs.cuda())
+        tc, tv, _, _, _ = vol.export_state()
+        kern = vol.kernel
+        vol.close()
+        m_c, m_v = blend.blend_means(rad.double().numpy(), dist.double().numpy(), dirs.double().numpy(), 6, 14, 50.0)
+        got_c = octahedral.interior(tc.double().numpy())
+        got_v = octahedral.interior(tv.double().numpy())
+
+        def rel(got, ref):
+            den = np.maximum(np.abs(ref), 1e-6 * np.max(np.abs(ref)))
+            e = np.abs(got - ref) / den
+            return {"max": float(e.max()), "mean": float(e.mean())}
+        out[form] = {"kernel": kern, "colour": rel(got_c, m_c), "visibility": rel(got_v, m_v),
+                     "vis_d": rel(got_v[0], m_v[0]), "vis_d2": rel(got_v[1], m_v[1])}
+    return {"workload": "16x16x16 probes, 256 rays, one noisy frame, h=0, FP32 state (texel = frame mean)",
+            "against": "FP64 oracle (oracle.blend.blend_means) on the operand-rounded inputs",
+            "tolerance": {"f32": 1e-5, "f16": 2e-3, "bf16": 2e-3}, "forms": out}
 
 
 def cpu_baseline(spec, seed, budget_s=12.0, max_frames=40):
@@ -702,6 +858,10 @@ def run_ours(args, ws, rank, local):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    if args.client_only:
+        if rank == 0:
+            print(json.dumps({"client": time_client(wl.config2(), wl.config_seed(2), hbm_peak, peak_src)}), flush=True)
+        return
     forms = [f for f in args.forms.split(",") if f]
     seed = wl.config_seed(2) + 1000 * rank
     results = {}
@@ -715,10 +875,13 @@ def run_ours(args, ws, rank, local):
     t_max = max_over_ranks(head["total_ms"], ws)
     P = 4096
     value = job_value(P, args.steps, ws, t_max)
-    op_bytes = 4 if forms[0] == "f32" else 2
-    bpp = blend_bytes_per_probe(256, op_bytes)
-    alg = bpp * P + (36 + 196) * 256 * 4
-    achieved = alg / (head["blend_ms"] / 1e3) / 1e9
+    def alg_bytes(form):
+        # shared weight images: F32 hi+lo float planes, BF16 hi+lo bfloat16, F16 one binary16 plane
+        wb = {"f32": 8, "bf16": 4, "f16": 2}[form]
+        return blend_bytes_per_probe(256, 4 if form == "f32" else 2) * P + (36 + 196) * 256 * wb
+    alg = alg_bytes(forms[0])
+    blend_ms = head["alone_ms"].get("blend", head["blend_ms"])
+    achieved = alg / (blend_ms / 1e3) / 1e9
     import hashlib
     src = os.path.join(ROOT, "paper_2103_05875_gb300", "csrc", "pv_blend_tc.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -733,15 +896,20 @@ def run_ours(args, ws, rank, local):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single volume",
                    "graphs": head["graphs"], "blend_kernel": head["kernel"]},
         "gpu_launches": head["launches_per_step"] * args.steps,
-        "breakdown_ms_per_step": {"weights": head["weights_ms"], "blend": head["blend_ms"],
-                                  "select_pack": head["select_pack_ms"]},
-        "forms": {f: {"value": P * args.steps / (r["total_ms"] / 1e3), "ms_per_step": r["total_ms"] / args.steps,
-                      "blend_ms": r["blend_ms"], "kernel": r["kernel"]} for f, r in results.items()},
+        "kernel_ms": {"alone": head["alone_ms"],
+                      "note": "each kernel in a graph of back-to-back launches, CUDA events around the replay; "
+                              "the chained step overlaps them (programmatic dependent launch)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "blend",
-                     "peak_source": peak_src, "algorithmic_bytes_per_launch": alg},
+                     "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "k_blend_tc",
+                     "launch_us": blend_ms * 1e3, "peak_source": peak_src, "algorithmic_bytes_per_launch": alg},
         "clocks": clk,
     }
+    forms_out = {}
+    for f, r in results.items():
+        bms = r["alone_ms"].get("blend", r["blend_ms"])
+        ach = alg_bytes(f) / (bms / 1e3) / 1e9
+        forms_out[f] = {"value": P * args.steps / (r["total_ms"] / 1e3), "ms_per_step": r["total_ms"] / args.steps,
+                        "blend_us": bms * 1e3, "blend_frac_of_hbm": ach / hbm_peak, "kernel": r["kernel"]}
     if not args.no_batched:
         line["batched"] = time_batched(max(10, args.steps // 2), args.warmup, seed)
     if rank == 0 and not args.no_served:
@@ -758,6 +926,11 @@ def run_ours(args, ws, rank, local):
                                                                "d2h_bytes_per_step")}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl.config2(), seed)
+    # last keys, so that a truncated copy of the line keeps them: the forms' rates
+    # and (rank 0, untimed, beside the CPU baseline) their accuracy against the oracle
+    line["forms"] = forms_out
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["accuracy"] = accuracy_report(wl.config_seed(3), tuple(forms))
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -196,6 +196,9 @@ __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, int* e
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
   return mbar_test(b, parity) || mbar_wait_slow(b, parity, err);
 }
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, int* err) {
+  return __all_sync(0xffffffffu, mbar_wait(b, parity, err));
+}
 __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, int* err) {
   if (mbar_try(b, parity)) return true;
   const unsigned long long t0 = gtime();
@@ -210,6 +213,18 @@ __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, int* e
     }
   }
 }
+// One lane of the (converged) warp; the issuing roles run their loops with the
+// whole warp, so that addresses and descriptors stay warp-uniform, and let the
+// elected lane issue the asynchronous instructions.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t p;
+  asm volatile(
+      "{\n .reg .b32 r;\n .reg .pred e;\n elect.sync r|e, 0xffffffff;\n selp.u32 %0, 1, 0, e;\n}\n"
+      : "=r"(p));
+  return p != 0;
+}
+// Bounded wait by every lane of a warp; the result is the same in all lanes.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, int* err);
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -652,24 +667,27 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     // ahead of the MMAs as the ray ring allows (no wait for the previous
     // kernel). Visibility chunk: d rows into lane quarter 0; colour chunk:
     // R, G, B rows into quarters 1..3.
-    if (lane == 0) {
+    if (elect_one()) {
       for (int v = 0; v < a.nvol; ++v) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].dist) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].rad) : "memory");
       }
-      int x = 0;
-      uint32_t ph = 0;
-      bool ok = true;
-      for (int it = 0; it < rounds && ok; ++it) {
-        const int item = blockIdx.x + it * gridDim.x;
-        const BlendVol& bv = a.v[vol_of(a, item)];
-        const int p0 = (item - bv.item0) * np;
-        for (int phase = 0; phase < 2 && ok; ++phase) {
-          for (int kc = 0; kc < bv.nchunks; ++kc) {
-            ok = mbar_wait(&xempty[x], ph ^ 1, err);
-            if (!ok) break;
-            uint8_t* st = xring + (size_t)x * tp.xstage;
-            const int xr = kc * tp.kc;
+    }
+    __syncwarp();
+    int x = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int it = 0; it < rounds && ok; ++it) {
+      const int item = blockIdx.x + it * gridDim.x;
+      const BlendVol& bv = a.v[vol_of(a, item)];
+      const int p0 = (item - bv.item0) * np;
+      for (int phase = 0; phase < 2 && ok; ++phase) {
+        for (int kc = 0; kc < bv.nchunks; ++kc) {
+          ok = mbar_wait_warp(&xempty[x], ph ^ 1, err);
+          if (!ok) break;
+          uint8_t* st = xring + (size_t)x * tp.xstage;
+          const int xr = kc * tp.kc;
+          if (elect_one()) {
             if (phase == 0) {
               mbar_expect_tx(&xfull[x], tp.tx_xv);
               tma_load_2d(st, &bv.dist, xr, p0, &xfull[x]);
@@ -678,10 +696,11 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
               for (int c = 0; c < 3; ++c)
                 tma_load_2d(st + (c + 1) * QROWS * ROWB, &bv.rad, xr, c * bv.k.P + p0, &xfull[x]);
             }
-            if (++x == tp.xs) {
-              x = 0;
-              ph ^= 1;
-            }
+          }
+          __syncwarp();
+          if (++x == tp.xs) {
+            x = 0;
+            ph ^= 1;
           }
         }
       }
@@ -691,88 +710,91 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     // The weight tile images (written by the weights kernel): visibility
     // chunk hi rows then lo rows; colour chunk hi then lo rows adjacent, so
     // that one MMA of N = 2 NCP takes both parts.
-    if (lane == 0) {
-      pv_grid_wait();
-      const uint32_t wvb = (uint32_t)S::NVP * ROWB, wcb = (uint32_t)S::NCP * ROWB;
-      int w = 0;
-      uint32_t ph = 0;
-      bool ok = true;
-      for (int it = 0; it < rounds && ok; ++it) {
-        const int item = blockIdx.x + it * gridDim.x;
-        const BlendVol& bv = a.v[vol_of(a, item)];
-        const size_t chunk_b = (size_t)bv.k.w_rows * ROWB;
-        const size_t plane_b = (size_t)bv.k.w_chunks * chunk_b;
-        for (int phase = 0; phase < 2 && ok; ++phase) {
-          for (int kc = 0; kc < bv.nchunks; ++kc) {
-            ok = mbar_wait(&wempty[w], ph ^ 1, err);
-            if (!ok) break;
-            const uint32_t st = smem_u32(wring + (size_t)w * tp.wstage);
-            const uint8_t* src = (const uint8_t*)bv.k.w_op + (size_t)kc * chunk_b + (phase == 0 ? 0 : wvb);
-            const uint32_t wb = phase == 0 ? wvb : wcb;
+    pv_grid_wait();
+    const uint32_t wvb = (uint32_t)S::NVP * ROWB, wcb = (uint32_t)S::NCP * ROWB;
+    int w = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int it = 0; it < rounds && ok; ++it) {
+      const int item = blockIdx.x + it * gridDim.x;
+      const BlendVol& bv = a.v[vol_of(a, item)];
+      const size_t chunk_b = (size_t)bv.k.w_rows * ROWB;
+      const size_t plane_b = (size_t)bv.k.w_chunks * chunk_b;
+      for (int phase = 0; phase < 2 && ok; ++phase) {
+        for (int kc = 0; kc < bv.nchunks; ++kc) {
+          ok = mbar_wait_warp(&wempty[w], ph ^ 1, err);
+          if (!ok) break;
+          const uint32_t st = smem_u32(wring + (size_t)w * tp.wstage);
+          const uint8_t* src = (const uint8_t*)bv.k.w_op + (size_t)kc * chunk_b + (phase == 0 ? 0 : wvb);
+          const uint32_t wb = phase == 0 ? wvb : wcb;
+          if (elect_one()) {
             mbar_expect_tx(&wfull[w], phase == 0 ? tp.tx_wv : tp.tx_wc);
             bulk_g2s(st, src, wb, &wfull[w]);
             if (kSplitW) bulk_g2s(st + wb, src + plane_b, wb, &wfull[w]);
-            if (++w == tp.ws) {
-              w = 0;
-              ph ^= 1;
-            }
+          }
+          __syncwarp();
+          if (++w == tp.ws) {
+            w = 0;
+            ph ^= 1;
           }
         }
       }
     }
   } else if (warp == 3) {
     // ------------------------------------------------------------ MMA issuer
-    // (on the fourth SMSP, which the visibility epilogue does not use)
-    if (lane == 0) {
-      int x = 0, w = 0, sa = 0;
-      uint32_t xph = 0, wph = 0, aph = 0, tph[2] = {0u, 0u};
-      uint32_t cvph = 0;                             // 16-bit: next d^2 phase parity per ray stage (bit x)
-      bool ok = true;
-      for (int it = 0; it < rounds && ok; ++it) {
-        const int item = blockIdx.x + it * gridDim.x;
-        const int nchunks = a.v[vol_of(a, item)].nchunks;
-        for (int phase = 0; phase < 2 && ok; ++phase) {
-          ok = mbar_wait(&tempty[phase], tph[phase] ^ 1, err);
+    // (on the fourth SMSP, which the visibility epilogue does not use). The
+    // whole warp runs the loop; one elected lane issues the MMAs and their
+    // commits (a commit tracks the MMAs of its own thread: the same lane).
+    int x = 0, w = 0, sa = 0;
+    uint32_t xph = 0, wph = 0, aph = 0, tph[2] = {0u, 0u};
+    uint32_t cvph = 0;                               // 16-bit: next d^2 phase parity per ray stage (bit x)
+    bool ok = true;
+    for (int it = 0; it < rounds && ok; ++it) {
+      const int item = blockIdx.x + it * gridDim.x;
+      const int nchunks = a.v[vol_of(a, item)].nchunks;
+      for (int phase = 0; phase < 2 && ok; ++phase) {
+        ok = mbar_wait_warp(&tempty[phase], tph[phase] ^ 1, err);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (phase == 0 ? 0u : (uint32_t)S::CBASE);
+        const uint32_t idesc = phase == 0 ? tp.idesc_v : tp.idesc_c;
+        for (int kc = 0; kc < nchunks; ++kc) {
+          // ray tiles ready: F32 in TMEM (converters); 16-bit visibility
+          // chunks once d^2 is written, colour chunks as soon as they land
+          if (kTmemA) {
+            ok = mbar_wait_warp(&afull[sa], aph, err);
+          } else if (phase == 0) {
+            ok = mbar_wait_warp(&xconv[x], (cvph >> x) & 1u, err);
+            cvph ^= 1u << x;
+          } else {
+            ok = mbar_wait_warp(&xfull[x], xph, err);
+          }
+          if (ok) ok = mbar_wait_warp(&wfull[w], wph, err);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t d = tmem + (phase == 0 ? 0u : (uint32_t)S::CBASE);
-          const uint32_t idesc = phase == 0 ? tp.idesc_v : tp.idesc_c;
-          for (int kc = 0; kc < nchunks; ++kc) {
-            // ray tiles ready: F32 in TMEM (converters); 16-bit visibility
-            // chunks once d^2 is written, colour chunks as soon as they land
-            if (kTmemA) {
-              ok = mbar_wait(&afull[sa], aph, err);
-            } else if (phase == 0) {
-              ok = mbar_wait(&xconv[x], (cvph >> x) & 1u, err);
-              cvph ^= 1u << x;
-            } else {
-              ok = mbar_wait(&xfull[x], xph, err);
-            }
-            if (ok) ok = mbar_wait(&wfull[w], wph, err);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t wb = smem_u32(wring + (size_t)w * tp.wstage);
-            const uint32_t xa = smem_u32(xring + (size_t)x * tp.xstage);
+          const uint32_t wb = smem_u32(wring + (size_t)w * tp.wstage);
+          const uint32_t xa = smem_u32(xring + (size_t)x * tp.xstage);
+          if (elect_one()) {
 #pragma unroll
-            for (int ks = 0; ks < ROWB / 32; ++ks) {            // one MMA K step per 32 bytes of row
+            for (int ks = 0; ks < ROWB / 32; ++ks) {          // one MMA K step per 32 bytes of row
               const uint32_t kb = 32u * ks;
               const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
               const uint64_t bw = sdesc(wb + kb);
               if constexpr (kTmemA) {
                 const uint32_t ah = tmem + (uint32_t)tp.abase + 32u * sa + 8u * ks;
-                if (phase == 0) {                                              // lanes hold hi and lo parts
-                  mma_ts_tf32(d, ah, bw, idesc, acc);                          // [d, d^2] (hi | lo) * W hi
-                  mma_ts_tf32(d, ah, sdesc(wb + WLO_V + kb), idesc, 1u);       // ... * W lo
+                if (phase == 0) {                                            // lanes hold hi and lo parts
+                  mma_ts_tf32(d, ah, bw, idesc, acc);                        // [d, d^2] (hi | lo) * W hi
+                  mma_ts_tf32(d, ah, sdesc(wb + WLO_V + kb), idesc, 1u);     // ... * W lo
                 } else {
-                  mma_ts_tf32(d, ah, bw, tp.idesc_c2, acc);                    // x hi * [W hi | W lo]
-                  mma_ts_tf32(d, ah + 16u, bw, idesc, 1u);                     // x lo * W hi
+                  mma_ts_tf32(d, ah, bw, tp.idesc_c2, acc);                  // x hi * [W hi | W lo]
+                  mma_ts_tf32(d, ah + 16u, bw, idesc, 1u);                   // x lo * W hi
                 }
               } else {
                 const uint64_t ax = sdesc(xa + kb);
                 if (kSplitW && phase == 1) {
-                  mma_ss<FORM>(d, ax, bw, tp.idesc_c2, acc);                   // x * [W hi | W lo]
+                  mma_ss<FORM>(d, ax, bw, tp.idesc_c2, acc);                 // x * [W hi | W lo]
                 } else {
-                  mma_ss<FORM>(d, ax, bw, idesc, acc);                         // visibility: d, d^2 hi, d^2 lo
+                  mma_ss<FORM>(d, ax, bw, idesc, acc);                       // visibility: d, d^2 hi, d^2 lo
                   if (kSplitW) mma_ss<FORM>(d, ax, sdesc(wb + WLO_V + kb), idesc, 1u);
                 }
               }
@@ -781,23 +803,25 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
             if constexpr (kTmemA) mma_commit(&aempty[sa]);
             else mma_commit(&xempty[x]);
             mma_commit(&wempty[w]);
-            if (++x == tp.xs) {
-              x = 0;
-              xph ^= 1;
-            }
-            if (++w == tp.ws) {
-              w = 0;
-              wph ^= 1;
-            }
-            if (kTmemA && ++sa == tp.as_) {
-              sa = 0;
-              aph ^= 1;
-            }
           }
-          if (!ok) break;
-          mma_commit(&tfull[phase]);                             // accumulators ready for the epilogue
-          tph[phase] ^= 1;
+          __syncwarp();
+          if (++x == tp.xs) {
+            x = 0;
+            xph ^= 1;
+          }
+          if (++w == tp.ws) {
+            w = 0;
+            wph ^= 1;
+          }
+          if (kTmemA && ++sa == tp.as_) {
+            sa = 0;
+            aph ^= 1;
+          }
         }
+        if (!ok) break;
+        if (elect_one()) mma_commit(&tfull[phase]);              // accumulators ready for the epilogue
+        __syncwarp();
+        tph[phase] ^= 1;
       }
     }
   } else if (warp >= 4 && warp < 8) {
