@@ -101,6 +101,11 @@ typedef struct pv_volume_info {
   int32_t kernel;                               /* blend kernel actually used */
   int32_t state_bytes_per_texel;
   uint64_t device_bytes;                        /* device memory the volume holds */
+  int32_t* error_word;                          /* device int32, non-zero once a bounded wait
+                                                   of the tensor-core blend gave up; read and
+                                                   cleared by probe_select_and_pack with
+                                                   want_host_counts (diagnostics and tests may
+                                                   set it to exercise that path) */
 } pv_volume_info;
 
 /*
@@ -191,8 +196,11 @@ pv_status probe_update_blend(pv_volume* vol, const void* radiance, const void* d
  * codes to the last-transmitted textures. Asynchronous unless
  * want_host_counts != 0, in which case the call waits for the stream and
  * fills out->count_c / count_v, and returns PV_ERR_TIMEOUT if a bounded
- * wait inside the tensor-core blend kernel expired (its results are then
- * invalid; the volume stays usable). out: host pv_frame.
+ * wait inside the tensor-core blend kernel expired since the last such call
+ * (the volume's error word is set): the frames blended since then are
+ * invalid, the word is cleared on `stream` and the volume stays usable.
+ * Without want_host_counts the word is not read and stays set. out: host
+ * pv_frame.
  */
 pv_status probe_select_and_pack(pv_volume* vol, pv_frame* out, int32_t want_host_counts,
                                 void* stream);

@@ -50,7 +50,8 @@ class pv_volume_info(C.Structure):
                 ("color_width", C.c_int32), ("color_height", C.c_int32),
                 ("color_pitch_bytes", C.c_int32), ("vis_width", C.c_int32),
                 ("vis_height", C.c_int32), ("vis_pitch_bytes", C.c_int32), ("kernel", C.c_int32),
-                ("state_bytes_per_texel", C.c_int32), ("device_bytes", C.c_uint64)]
+                ("state_bytes_per_texel", C.c_int32), ("device_bytes", C.c_uint64),
+                ("error_word", C.c_void_p)]
 
 
 class pv_frame(C.Structure):

@@ -387,6 +387,7 @@ pv_status probe_volume_info(const pv_volume* v, pv_volume_info* o) {
   o->kernel = v->kernel;
   o->state_bytes_per_texel = L.sb;
   o->device_bytes = v->bytes;
+  o->error_word = v->k.err;
   return PV_OK;
 }
 
@@ -445,9 +446,13 @@ pv_status probe_select_and_pack(pv_volume* v, pv_frame* out, int32_t want_host_c
     if (e != cudaSuccess) return cuda_fail(e, "count readback");
     out->count_c = v->host_counts[0];
     out->count_v = v->host_counts[1];
-    if (v->host_counts[2])
+    if (v->host_counts[2]) {
+      // reported once: clear the word so that the next frames run normally
+      e = cudaMemsetAsync(v->k.err, 0, sizeof(int), st);
+      if (e != cudaSuccess) return cuda_fail(e, "error word reset");
       return pv_set_error(PV_ERR_TIMEOUT, "a bounded wait in the blend kernel expired (frame %llu)",
                           (unsigned long long)v->frame);
+    }
   }
   return PV_OK;
 }

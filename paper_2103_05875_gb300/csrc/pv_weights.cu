@@ -4,21 +4,34 @@
 // used for normalisation. One block per texel, threads over rays. Block 0
 // also clears the frame's changed-probe bits and sets the frame's hysteresis.
 //
+// Per-texel scale. The normalised mean sum_r W x_r / sum_r W does not change
+// when all of a texel's weights are multiplied by one factor, so each texel's
+// weights are taken relative to its largest cosine c_max: colour weights are
+// c scaled by the power of two that brings c_max into [1, 2) (exact),
+// visibility weights are (c / c_max)^s (the largest is 1). No weight of a
+// texel that sees any ray can then underflow, whatever the sharpness or the
+// operand format: a texel whose rays all lie more than ~83 degrees away would
+// otherwise get cos^50 below the smallest float32, and one beyond ~55 degrees
+// would get binary16 zeros. A texel keeps its old value (weight sum 0) only
+// when no ray lies in its hemisphere.
+//
 // Operand forms. FP32: the SIMT blend uses W as is; the tensor-core blend gets
 // W = hi + lo with hi = W truncated to TF32 and lo = W - hi (three TF32
 // products recover FP32 accuracy). FP16: W in binary16, visibility weights
-// scaled by 2^15 so that cos^s does not underflow (the scale cancels in the
-// normalisation). BF16: W = hi + lo, both bfloat16 (two products), since one
-// bfloat16 weight alone is only good to 2^-9. The weight sums always add the
-// effective (rounded) weights, so every texel's mean stays a convex combination.
+// scaled by 2^15 (the largest is then 2^15, and relative weights down to 2^-29
+// stay normal binary16 numbers). BF16: W = hi + lo, both bfloat16 (two
+// products), since one bfloat16 weight alone is only good to 2^-9. The weight
+// sums always add the effective (rounded) weights, so every texel's mean stays
+// a convex combination.
 //
 // Accuracy: the octahedral texel direction is q/|q| with an integer vector q
 // (u = a/n, v = b/n with integer a, b), so n_t . d_r is evaluated as a
 // float-float dot product of exact integers with the float32 ray directions,
 // divided by sqrt(|q|^2) in float-float. The cosine is then within half an
-// ulp, and the visibility weight c^s is corrected to first order for the low
-// part of c (s * c_lo / c_hi), which keeps the amplification of the cosine's
-// rounding by the exponent s out of W. Weights are rounded to the operand
+// ulp; the ratio c / c_max is formed as a float-float too, and the visibility
+// weight (c / c_max)^s is corrected to first order for the ratio's low part
+// (s * r_lo / r_hi), which keeps the amplification of rounding by the
+// exponent s out of W. Weights are rounded to the operand
 // format (FP16/BF16 precision forms) before they are summed, so each texel's
 // normalisation uses exactly the weights of the contraction.
 #include <cuda_bf16.h>
@@ -96,12 +109,14 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
   const float sq_lo = fmaf(-sq, sq, Q) / (2.0f * sq);   // sqrt(Q) ~= sq + sq_lo
   const float s = k.sharpness;
 
-  OpWeight o[kRaysPerThread];
-  float part = 0.0f;
+  // cosines of this thread's rays as float-floats, and the block's largest
+  float ch[kRaysPerThread], cl[kRaysPerThread];
+  float mh = -2.0f, ml = 0.0f;
 #pragma unroll
   for (int u = 0; u < kRaysPerThread; ++u) {
     const int r = threadIdx.x + 256 * u;
-    o[u] = OpWeight{0.0f, 0.0f, 0.0f};
+    ch[u] = -2.0f;
+    cl[u] = 0.0f;
     if (r >= k.R) continue;
     const float dx = dirs[3 * r + 0], dy = dirs[3 * r + 1], dz = dirs[3 * r + 2];
     float p1, e1, p2, e2, p3, e3, s12, f12, sd, f3;
@@ -115,13 +130,54 @@ __device__ __forceinline__ void weights_block(const pv_dev& k, const float* __re
     float rem = fmaf(-c0, sq, sd);                        // exact remainder of the division
     rem = (rem + sd_lo) - c0 * sq_lo;
     const float c1 = rem / sq;
-    float c_hi, c_lo;
-    two_sum(c0, c1, c_hi, c_lo);                          // cosine as a float-float
+    two_sum(c0, c1, ch[u], cl[u]);                        // cosine as a float-float
+    if (ch[u] > mh || (ch[u] == mh && cl[u] > ml)) {
+      mh = ch[u];
+      ml = cl[u];
+    }
+  }
+  // block maximum of the cosine (warp shuffles, then the warps' maxima in
+  // a fixed order: every thread ends with the same pair)
+  __shared__ float smax[2][8];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, mh, off), ol = __shfl_xor_sync(0xffffffffu, ml, off);
+    if (oh > mh || (oh == mh && ol > ml)) {
+      mh = oh;
+      ml = ol;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    smax[0][threadIdx.x >> 5] = mh;
+    smax[1][threadIdx.x >> 5] = ml;
+  }
+  __syncthreads();
+  mh = smax[0][0];
+  ml = smax[1][0];
+  for (int wi = 1; wi < 8; ++wi) {
+    if (smax[0][wi] > mh || (smax[0][wi] == mh && smax[1][wi] > ml)) {
+      mh = smax[0][wi];
+      ml = smax[1][wi];
+    }
+  }
+  const int ce = mh > 0.0f ? ilogbf(mh) : 0;               // colour: c * 2^-ce, largest in [1, 2)
+
+  OpWeight o[kRaysPerThread];
+  float part = 0.0f;
+#pragma unroll
+  for (int u = 0; u < kRaysPerThread; ++u) {
+    o[u] = OpWeight{0.0f, 0.0f, 0.0f};
+    const float c_hi = ch[u], c_lo = cl[u];
+    if (!(c_hi > 0.0f)) continue;                          // no ray, or a ray behind the texel
     float w;
     if (!vis) {
-      w = c_hi > 0.0f ? c_hi : 0.0f;
+      w = ldexpf(c_hi, -ce);
     } else {
-      w = c_hi > 0.0f ? powf(c_hi, s) * fmaf(s, c_lo / c_hi, 1.0f) : 0.0f;
+      // r = c / c_max as a float-float (the remainder of r0 * m_hi is exact)
+      const float r0 = c_hi / mh;
+      const float res = fmaf(-r0, mh, c_hi) + (c_lo - r0 * ml);
+      const float r1 = res / mh;
+      w = powf(r0, s) * fmaf(s, r1 / r0, 1.0f);
     }
     o[u] = split_weight(w, k.operand_fmt, vis);
     part += o[u].eff;
