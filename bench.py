@@ -36,7 +36,7 @@ FPG = 4          # frames per captured graph in the timed replays
 # DRAM bytes (read + write) of one k_blend_tc launch of the FP32 form from one ncu capture
 # of this workload, valid only for the kernel source it was taken on: reported as null once
 # the source has changed.
-BLEND_TRAFFIC = {"source_sha256_prefix": "c4839e0fa70e02d7", "f32": 27500288 + 256}
+BLEND_TRAFFIC = {"source_sha256_prefix": "1caf629332d22d1d", "f32": 27399936 + 0, "f16": 18616576 + 0}
 METRIC = "probes updated+packed/sec at 16^3 probes x 256 rays (plain FP32 form)"
 UNIT = "probes/s"
 WORKLOAD = "16x16x16 probes, 256 rays/probe, colour 6x6+1, vis 14x14+1, FP16 state, h=0.97, s=50"
@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-client", action="store_true")
     ap.add_argument("--no-views", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=20.0)
+    ap.add_argument("--blend-only", action="store_true",
+                    help="run --steps eager frames (weights, blend, select/pack) of the first of --forms after "
+                         "--warmup frames, no graphs, and print their wall time: the command the kernel "
+                         "profiles are taken with")
     ap.add_argument("--client-only", action="store_true",
                     help="time only the client decode (L2 flushed before each launch) and print its object")
     return ap.parse_args()
@@ -169,6 +173,28 @@ def make_inputs(spec, seed, nbuf):
         dirs = torch.from_numpy(fs.directions(f)).cuda()
         bufs.append((rad, dist, dirs))
     return fs, bufs
+
+
+def eager_frames(spec, steps, warmup, seed):
+    """Plain eager frames on the default stream (a small, fixed launch sequence for profilers)."""
+    import torch
+    import paper_2103_05875_gb300 as pv
+    fs, bufs = make_inputs(spec, seed, NBUF)
+    vol = pv.ProbeVolume(spec)
+    for s in range(warmup):
+        vol.update(*bufs[s % NBUF])
+        vol.select_and_pack()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for s in range(steps):
+        vol.update(*bufs[(warmup + s) % NBUF])
+        vol.select_and_pack()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    out = {"workload": f"{spec.nx}x{spec.ny}x{spec.nz} probes, {spec.rays} rays, {spec.operand_fmt} operands",
+           "kernel": vol.kernel, "frames": steps, "wall_us_per_frame": dt / max(steps, 1) * 1e6}
+    vol.close()
+    return out
 
 
 def time_form(spec, steps, warmup, seed):
@@ -858,6 +884,11 @@ def run_ours(args, ws, rank, local):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    if args.blend_only:
+        if rank == 0:
+            print(json.dumps({"blend_only": eager_frames(wl.config2(operand_fmt=args.forms.split(",")[0]),
+                                                          args.steps, args.warmup, wl.config_seed(2))}), flush=True)
+        return
     if args.client_only:
         if rank == 0:
             print(json.dumps({"client": time_client(wl.config2(), wl.config_seed(2), hbm_peak, peak_src)}), flush=True)

@@ -90,7 +90,13 @@ constexpr int EPI_THREADS = 256;         // warps 8..15
 // two buffers per warp pair
 constexpr uint32_t XROW_BYTES = 2 * 14 * 4;
 constexpr uint32_t XBUF_BYTES = 32 * XROW_BYTES;
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+// Bound of every mbarrier wait, in SM clock cycles: 4e9 is 2 s at 2 GHz
+// (1.9 s at the 2.07 GHz maximum, longer at lower clocks).
+constexpr long long kWaitCycles = 4000000000ll;
+// Chunk rings: per K chunk n (counted over the CTA's run) one "ready" barrier
+// (operands in place) and one "done" barrier (the chunk's MMAs completed), in
+// rings of kRing; slot n % kRing, phase parity (n / kRing) % 2.
+constexpr int kRing = 16;
 // binary16 operand form: d^2 enters the MMA scaled by 2^-4 (exact), which
 // keeps the high part of d^2 for hit distances up to 2^10 in binary16 range
 constexpr float kD2ScaleF16 = 0.0625f;
@@ -132,6 +138,8 @@ struct BlendVol {
   CUtensorMap last_v, last_c;            // last-transmitted codes (read)
   CUtensorMap cur_v, cur_c;              // current codes (written)
   pv_dev k;
+  const uint8_t* rad_g;                  // the same rays as plain pointers (L2 prefetch)
+  const uint8_t* dist_g;
   int item0;                             // first work item of the volume in the launch
   int nchunks;                           // ray chunks of kc rays
 };
@@ -153,11 +161,6 @@ __device__ __forceinline__ int vol_of(const BlendArgs<MAXV>& a, int item) {
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long gtime() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
 }
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
@@ -197,17 +200,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err
   return mbar_test(b, parity) || mbar_wait_slow(b, parity, err);
 }
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, int* err) {
-  return __all_sync(0xffffffffu, mbar_wait(b, parity, err));
+  // the common case (phase already complete) through a non-blocking test and a
+  // vote, so that the branch around the bounded wait is warp-uniform
+  if (__all_sync(0xffffffffu, mbar_test(b, parity))) return true;
+  return __all_sync(0xffffffffu, mbar_wait_slow(b, parity, err));
+}
+// The MMAs of chunk m are complete (always true for m < 0). A role refilling a
+// stage last read by chunk m waits here; a later phase of the same slot cannot
+// mislead the parity test, since chunk m + kRing needs the stage refilled first.
+__device__ __forceinline__ bool wait_done_warp(uint64_t* done, int m, int* err) {
+  return m < 0 || mbar_wait_warp(&done[m & (kRing - 1)], (uint32_t)((m / kRing) & 1), err);
 }
 __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, int* err) {
+  // The deadline is kept with the SM's cycle counter: reading the global
+  // timer costs hundreds of cycles, which every wait that blocks would pay
+  // before it could see its phase complete.
   if (mbar_try(b, parity)) return true;
-  const unsigned long long t0 = gtime();
+  const long long t0 = clock64();
   for (;;) {
 #pragma unroll 1
-    for (int i = 0; i < 128; ++i)
+    for (int i = 0; i < 64; ++i)
       if (mbar_try(b, parity)) return true;
     if (*(volatile int*)err) return false;
-    if (gtime() - t0 > kWaitNs) {
+    if (clock64() - t0 > kWaitCycles) {
       atomicExch(err, 1);
       return false;
     }
@@ -267,6 +282,10 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+// Contiguous global bytes into L2 (16-byte aligned start and size).
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read() {
@@ -611,14 +630,11 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   constexpr uint32_t TBV = (uint32_t)((NV + 2) * (NV + 2) * SB), TBC = (uint32_t)((NC + 2) * (NC + 2) * SB);
   constexpr uint32_t WLO_V = (uint32_t)S::NVP * ROWB;              // visibility lo plane offset in a weight stage
 
-  uint64_t* xfull = (uint64_t*)(smem + tp.off_bar);  // [xs] ray tiles landed
-  uint64_t* xconv = xfull + tp.xs;                   // [xs] 16-bit forms: d^2 parts written
-  uint64_t* xempty = xconv + tp.xs;                  // [xs] ray stage free
-  uint64_t* wfull = xempty + tp.xs;                  // [ws] weight tiles landed
-  uint64_t* wempty = wfull + tp.ws;                  // [ws] weight stage free
-  uint64_t* afull = wempty + tp.ws;                  // [as] F32: TMEM A stage written
-  uint64_t* aempty = afull + tp.as_;                 // [as] F32: TMEM A stage free
-  uint64_t* tfull = aempty + tp.as_;                 // [2] visibility, colour accumulators ready
+  uint64_t* xfull = (uint64_t*)(smem + tp.off_bar);  // [xs] ray tiles landed (for the converters)
+  uint64_t* xempty = xfull + tp.xs;                  // [xs] F32: ray stage converted, free
+  uint64_t* ready = xempty + tp.xs;                  // [kRing] chunk's operands in place
+  uint64_t* done = ready + kRing;                    // [kRing] chunk's MMAs completed
+  uint64_t* tfull = done + kRing;                    // [2] visibility, colour accumulators ready
   uint64_t* tempty = tfull + 2;                      // [2] accumulators drained
   uint64_t* efull = tempty + 2;                      // [2] an item's old texels and codes arrived
   uint32_t* tmem_holder = (uint32_t*)(efull + 2);
@@ -626,16 +642,14 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
   if (threadIdx.x == 0) {
     for (int i = 0; i < tp.xs; ++i) {
       mbar_init(&xfull[i], 1);
-      mbar_init(&xconv[i], 4);                       // the four converter warps
-      mbar_init(&xempty[i], kTmemA ? 4 : 1);         // converters (F32) or the MMAs (16-bit)
+      mbar_init(&xempty[i], 4);                      // the four converter warps (F32)
     }
-    for (int i = 0; i < tp.ws; ++i) {
-      mbar_init(&wfull[i], 1);
-      mbar_init(&wempty[i], 1);
-    }
-    for (int i = 0; i < tp.as_; ++i) {
-      mbar_init(&afull[i], 4);
-      mbar_init(&aempty[i], 1);
+    // ready: the weight producer's expect-tx arrival plus four more, from the
+    // converters (F32 chunks, 16-bit visibility chunks) or from the ray
+    // producer (16-bit colour chunks, whose tiles land on this barrier)
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(&ready[i], 5);
+      mbar_init(&done[i], 1);                        // the MMA thread's commit
     }
     for (int b = 0; b < 2; ++b) mbar_init(&tfull[b], 1);
     mbar_init(&tempty[0], kTmemA ? 8 : 6);           // visibility epilogue warps and their partners
@@ -674,16 +688,38 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
       }
     }
     __syncwarp();
-    int x = 0;
+    // A stage is free once the converters hold its rays (F32: in TMEM) or
+    // once the MMAs that read it completed (16-bit). Tiles land on xfull for
+    // the converters, except 16-bit colour tiles, which the MMAs read as they
+    // are: those land on the chunk's ready barrier, and this thread adds the
+    // four arrivals the converters would have made.
+    // Each item's ray rows are contiguous per channel (the item's probes are
+    // consecutive): they are prefetched into L2 whole, one item ahead, so
+    // that HBM streams full rows while the chunk tiles (64-byte slices of
+    // every row) are read from L2.
+    auto prefetch_item = [&](int item) {
+      const BlendVol& bv = a.v[vol_of(a, item)];
+      const int p0 = (item - bv.item0) * np, npi = min(np, bv.k.P - p0);
+      const size_t rb = (size_t)bv.k.R * (kTmemA ? 4 : 2);
+      const uint32_t bytes = (uint32_t)(npi * rb);
+      prefetch_l2(bv.dist_g + (size_t)p0 * rb, bytes);
+      for (int c = 0; c < 3; ++c) prefetch_l2(bv.rad_g + ((size_t)c * bv.k.P + p0) * rb, bytes);
+    };
+    if (rounds > 0 && elect_one()) prefetch_item(blockIdx.x);
+    __syncwarp();
+    int x = 0, n = 0;
     uint32_t ph = 0;
     bool ok = true;
     for (int it = 0; it < rounds && ok; ++it) {
       const int item = blockIdx.x + it * gridDim.x;
       const BlendVol& bv = a.v[vol_of(a, item)];
       const int p0 = (item - bv.item0) * np;
+      if (it + 1 < rounds && elect_one()) prefetch_item(item + gridDim.x);
+      __syncwarp();
       for (int phase = 0; phase < 2 && ok; ++phase) {
-        for (int kc = 0; kc < bv.nchunks; ++kc) {
-          ok = mbar_wait_warp(&xempty[x], ph ^ 1, err);
+        for (int kc = 0; kc < bv.nchunks; ++kc, ++n) {
+          if (kTmemA) ok = mbar_wait_warp(&xempty[x], ph ^ 1, err);
+          else ok = wait_done_warp(done, n - tp.xs, err);
           if (!ok) break;
           uint8_t* st = xring + (size_t)x * tp.xstage;
           const int xr = kc * tp.kc;
@@ -692,9 +728,12 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
               mbar_expect_tx(&xfull[x], tp.tx_xv);
               tma_load_2d(st, &bv.dist, xr, p0, &xfull[x]);
             } else {
-              mbar_expect_tx(&xfull[x], tp.tx_xc);
+              uint64_t* b = kTmemA ? &xfull[x] : &ready[n & (kRing - 1)];
+              mbar_expect_tx(b, tp.tx_xc);
+              if (!kTmemA)
+                for (int i = 0; i < 3; ++i) mbar_arrive(b);
               for (int c = 0; c < 3; ++c)
-                tma_load_2d(st + (c + 1) * QROWS * ROWB, &bv.rad, xr, c * bv.k.P + p0, &xfull[x]);
+                tma_load_2d(st + (c + 1) * QROWS * ROWB, &bv.rad, xr, c * bv.k.P + p0, b);
             }
           }
           __syncwarp();
@@ -712,8 +751,9 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     // that one MMA of N = 2 NCP takes both parts.
     pv_grid_wait();
     const uint32_t wvb = (uint32_t)S::NVP * ROWB, wcb = (uint32_t)S::NCP * ROWB;
-    int w = 0;
-    uint32_t ph = 0;
+    // Tiles land on the chunk's ready barrier; a stage is refilled once the
+    // MMAs of the chunk that last read it completed.
+    int w = 0, n = 0;
     bool ok = true;
     for (int it = 0; it < rounds && ok; ++it) {
       const int item = blockIdx.x + it * gridDim.x;
@@ -721,22 +761,20 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
       const size_t chunk_b = (size_t)bv.k.w_rows * ROWB;
       const size_t plane_b = (size_t)bv.k.w_chunks * chunk_b;
       for (int phase = 0; phase < 2 && ok; ++phase) {
-        for (int kc = 0; kc < bv.nchunks; ++kc) {
-          ok = mbar_wait_warp(&wempty[w], ph ^ 1, err);
+        for (int kc = 0; kc < bv.nchunks; ++kc, ++n) {
+          ok = wait_done_warp(done, n - tp.ws, err);
           if (!ok) break;
           const uint32_t st = smem_u32(wring + (size_t)w * tp.wstage);
           const uint8_t* src = (const uint8_t*)bv.k.w_op + (size_t)kc * chunk_b + (phase == 0 ? 0 : wvb);
           const uint32_t wb = phase == 0 ? wvb : wcb;
           if (elect_one()) {
-            mbar_expect_tx(&wfull[w], phase == 0 ? tp.tx_wv : tp.tx_wc);
-            bulk_g2s(st, src, wb, &wfull[w]);
-            if (kSplitW) bulk_g2s(st + wb, src + plane_b, wb, &wfull[w]);
+            uint64_t* b = &ready[n & (kRing - 1)];
+            mbar_expect_tx(b, phase == 0 ? tp.tx_wv : tp.tx_wc);
+            bulk_g2s(st, src, wb, b);
+            if (kSplitW) bulk_g2s(st + wb, src + plane_b, wb, b);
           }
           __syncwarp();
-          if (++w == tp.ws) {
-            w = 0;
-            ph ^= 1;
-          }
+          if (++w == tp.ws) w = 0;
         }
       }
     }
@@ -745,9 +783,15 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     // (on the fourth SMSP, which the visibility epilogue does not use). The
     // whole warp runs the loop; one elected lane issues the MMAs and their
     // commits (a commit tracks the MMAs of its own thread: the same lane).
-    int x = 0, w = 0, sa = 0;
-    uint32_t xph = 0, wph = 0, aph = 0, tph[2] = {0u, 0u};
-    uint32_t cvph = 0;                               // 16-bit: next d^2 phase parity per ray stage (bit x)
+    // One wait per chunk (its ready barrier) and one commit (its done
+    // barrier, which frees its ray, TMEM and weight stages together).
+    // Descriptors advance by stage offsets: a shared-memory descriptor holds
+    // address / 16 in its low bits, and every address stays below 2^18.
+    int x = 0, w = 0, sa = 0, n = 0;
+    uint32_t tph[2] = {0u, 0u};
+    const uint64_t wdesc0 = sdesc(smem_u32(wring)), xdesc0 = sdesc(smem_u32(xring));
+    const uint32_t wst16 = (uint32_t)tp.wstage >> 4, xst16 = (uint32_t)tp.xstage >> 4;
+    const uint32_t abase = tmem + (uint32_t)tp.abase;
     bool ok = true;
     for (int it = 0; it < rounds && ok; ++it) {
       const int item = blockIdx.x + it * gridDim.x;
@@ -758,65 +802,42 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         tc_fence_after();
         const uint32_t d = tmem + (phase == 0 ? 0u : (uint32_t)S::CBASE);
         const uint32_t idesc = phase == 0 ? tp.idesc_v : tp.idesc_c;
-        for (int kc = 0; kc < nchunks; ++kc) {
-          // ray tiles ready: F32 in TMEM (converters); 16-bit visibility
-          // chunks once d^2 is written, colour chunks as soon as they land
-          if (kTmemA) {
-            ok = mbar_wait_warp(&afull[sa], aph, err);
-          } else if (phase == 0) {
-            ok = mbar_wait_warp(&xconv[x], (cvph >> x) & 1u, err);
-            cvph ^= 1u << x;
-          } else {
-            ok = mbar_wait_warp(&xfull[x], xph, err);
-          }
-          if (ok) ok = mbar_wait_warp(&wfull[w], wph, err);
+        for (int kc = 0; kc < nchunks; ++kc, ++n) {
+          ok = mbar_wait_warp(&ready[n & (kRing - 1)], (uint32_t)((n / kRing) & 1), err);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t wb = smem_u32(wring + (size_t)w * tp.wstage);
-          const uint32_t xa = smem_u32(xring + (size_t)x * tp.xstage);
+          const uint64_t bw0 = wdesc0 + (uint64_t)(w * wst16);
+          const uint64_t ax0 = xdesc0 + (uint64_t)(x * xst16);
           if (elect_one()) {
 #pragma unroll
             for (int ks = 0; ks < ROWB / 32; ++ks) {          // one MMA K step per 32 bytes of row
-              const uint32_t kb = 32u * ks;
               const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-              const uint64_t bw = sdesc(wb + kb);
+              const uint64_t bw = bw0 + 2u * ks;                // + 32 bytes
               if constexpr (kTmemA) {
-                const uint32_t ah = tmem + (uint32_t)tp.abase + 32u * sa + 8u * ks;
+                const uint32_t ah = abase + 32u * sa + 8u * ks;
                 if (phase == 0) {                                            // lanes hold hi and lo parts
                   mma_ts_tf32(d, ah, bw, idesc, acc);                        // [d, d^2] (hi | lo) * W hi
-                  mma_ts_tf32(d, ah, sdesc(wb + WLO_V + kb), idesc, 1u);     // ... * W lo
+                  mma_ts_tf32(d, ah, bw + (WLO_V >> 4), idesc, 1u);          // ... * W lo
                 } else {
                   mma_ts_tf32(d, ah, bw, tp.idesc_c2, acc);                  // x hi * [W hi | W lo]
                   mma_ts_tf32(d, ah + 16u, bw, idesc, 1u);                   // x lo * W hi
                 }
               } else {
-                const uint64_t ax = sdesc(xa + kb);
+                const uint64_t ax = ax0 + 2u * ks;
                 if (kSplitW && phase == 1) {
                   mma_ss<FORM>(d, ax, bw, tp.idesc_c2, acc);                 // x * [W hi | W lo]
                 } else {
                   mma_ss<FORM>(d, ax, bw, idesc, acc);                       // visibility: d, d^2 hi, d^2 lo
-                  if (kSplitW) mma_ss<FORM>(d, ax, sdesc(wb + WLO_V + kb), idesc, 1u);
+                  if (kSplitW) mma_ss<FORM>(d, ax, bw + (WLO_V >> 4), idesc, 1u);
                 }
               }
             }
-            // stages free once these MMAs finish
-            if constexpr (kTmemA) mma_commit(&aempty[sa]);
-            else mma_commit(&xempty[x]);
-            mma_commit(&wempty[w]);
+            mma_commit(&done[n & (kRing - 1)]);                 // the chunk's stages free once these finish
           }
           __syncwarp();
-          if (++x == tp.xs) {
-            x = 0;
-            xph ^= 1;
-          }
-          if (++w == tp.ws) {
-            w = 0;
-            wph ^= 1;
-          }
-          if (kTmemA && ++sa == tp.as_) {
-            sa = 0;
-            aph ^= 1;
-          }
+          if (++x == tp.xs) x = 0;
+          if (++w == tp.ws) w = 0;
+          if (kTmemA && ++sa == tp.as_) sa = 0;
         }
         if (!ok) break;
         if (elect_one()) mma_commit(&tfull[phase]);              // accumulators ready for the epilogue
@@ -826,15 +847,19 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     }
   } else if (warp >= 4 && warp < 8) {
     // ------------------------------------------------------------ converters
+    // Each converter warp arrives once on the chunk's ready barrier when its
+    // part is written (16-bit colour chunks need no conversion: the ray
+    // producer arrives for them).
     const int q = warp & 3;
-    int x = 0, sa = 0;
-    uint32_t ph = 0, aph = 0;
+    int x = 0, sa = 0, n = 0;
+    uint32_t ph = 0;
     bool ok = true;
     for (int it = 0; it < rounds && ok; ++it) {
       const int item = blockIdx.x + it * gridDim.x;
       const int nchunks = a.v[vol_of(a, item)].nchunks;
       for (int phase = 0; phase < 2 && ok; ++phase) {
-        if (!kTmemA && phase == 1) {                 // 16-bit colour chunks need no conversion
+        if (!kTmemA && phase == 1) {
+          n += nchunks;
           x += nchunks;
           while (x >= tp.xs) {
             x -= tp.xs;
@@ -842,8 +867,8 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
           }
           continue;
         }
-        for (int kc = 0; kc < nchunks; ++kc) {
-          ok = mbar_wait(&xfull[x], ph, err);
+        for (int kc = 0; kc < nchunks; ++kc, ++n) {
+          ok = mbar_wait_warp(&xfull[x], ph, err);
           if (!ok) break;
           const uint32_t sx = smem_u32(xring + (size_t)x * tp.xstage);
           if constexpr (kTmemA) {
@@ -853,7 +878,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
             // MMA takes both parts and the epilogue adds quarter 2 to 0 and 3
             // to 1. Colour: q1..q3 = R, G, B, hi in the first 16 columns and
             // lo in the next 16.
-            ok = mbar_wait(&aempty[sa], aph ^ 1, err);
+            ok = wait_done_warp(done, n - tp.as_, err);      // the MMAs that read this TMEM stage
             if (!ok) break;
             tc_fence_after();
             if (phase == 0 || q >= 1) {
@@ -887,13 +912,10 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-              mbar_arrive(&afull[sa]);
               mbar_arrive(&xempty[x]);
+              mbar_arrive(&ready[n & (kRing - 1)]);
             }
-            if (++sa == tp.as_) {
-              sa = 0;
-              aph ^= 1;
-            }
+            if (++sa == tp.as_) sa = 0;
           } else {
             // d^2 = hi + lo in the operand format (binary16 scaled by 2^-4):
             // the hi part into lane quarter 1 of the A tile, the lo part into
@@ -936,7 +958,7 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
               fence_proxy_async();
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&xconv[x]);
+            if (lane == 0) mbar_arrive(&ready[n & (kRing - 1)]);
           }
           if (++x == tp.xs) {
             x = 0;
@@ -1331,6 +1353,8 @@ cudaError_t encode_ray_maps(const pv_dev& k, int form, const TcParams& tp, const
   const int ob = form == kF32 ? 4 : 2;
   cudaError_t e = encode_2d(&bv.rad, k.operand_fmt, rad, k.R, (uint64_t)3 * k.P, (uint64_t)k.R * ob, tp.kc, tp.np);
   if (e == cudaSuccess) e = encode_2d(&bv.dist, k.operand_fmt, dist, k.R, k.P, (uint64_t)k.R * ob, tp.kc, tp.np);
+  bv.rad_g = (const uint8_t*)rad;
+  bv.dist_g = (const uint8_t*)dist;
   return e;
 }
 
