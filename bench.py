@@ -459,7 +459,6 @@ def time_batched(steps, warmup, seed, operand_fmt="f32"):
     batch = pv.ProbeBatch(vols)
     np_auto = batch.probes_per_item
     args0 = ([x[0] for x in frames[0]], [x[1] for x in frames[0]], [x[2] for x in frames[0]])
-    np_tuned = batch.tune(*args0, reps=3)
 
     def bstep(f):
         def run():
@@ -467,7 +466,21 @@ def time_batched(steps, warmup, seed, operand_fmt="f32"):
             batch.update([x[0] for x in ins], [x[1] for x in ins], [x[2] for x in ins])
             batch.select_and_pack()
         return run
+    ms_default = _graph_steps([bstep(0), bstep(1)], steps, warmup)
+    # tune into a fresh cache file, then show that a second batch of the same shapes is
+    # answered from it without timing
+    cache_dir = tempfile.mkdtemp(prefix="pv_tune_")
+    cache = os.path.join(cache_dir, "tune.txt")
+    tuned = batch.autotune(*args0, reps=5, cache_path=cache)
     ms_b = _graph_steps([bstep(0), bstep(1)], steps, warmup)
+    vols2 = [pv.ProbeVolume(s) for s in specs]
+    batch2 = pv.ProbeBatch(vols2)
+    again = batch2.autotune(*args0, reps=5, cache_path=cache)
+    batch2.close()
+    for v in vols2:
+        v.close()
+    os.remove(cache)
+    os.rmdir(cache_dir)
     singles = [pv.ProbeVolume(s) for s in specs]
 
     def sstep(f):
@@ -480,7 +493,15 @@ def time_batched(steps, warmup, seed, operand_fmt="f32"):
     out = {"workload": "12 volumes 8x4x8 .. 32x8x32 (37,376 probes), rays 128/192/256, FP16 state, "
                        f"{operand_fmt} operands, noisy", "probes_per_step": P,
            "value": P * steps / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / steps,
-           "probes_per_item": {"default": np_auto, "tuned": np_tuned},
+           "probes_per_item": {"default": np_auto, "tuned": tuned["probes_per_item"]},
+           "default_plan": {"value": P * steps / (ms_default / 1e3), "ms_per_step": ms_default / steps},
+           "tuned_plan": {k: tuned[k] for k in ("probes_per_item", "ray_stages", "weight_stages", "tmem_stages",
+                                                "ctas", "candidates")},
+           "tuner_blend_us": {"default": tuned["default_us"], "tuned": tuned["best_us"]},
+           "tuner_cache": {"second_batch_from_cache": bool(again["from_cache"]),
+                           "second_batch_plan_equal": all(again[k] == tuned[k] for k in
+                                                          ("probes_per_item", "ray_stages", "weight_stages",
+                                                           "tmem_stages", "ctas"))},
            "launches_per_step": 3,
            "volume_by_volume": {"value": P * steps / (ms_s / 1e3), "ms_per_step": ms_s / steps,
                                 "launches_per_step": 3 * len(specs)}}

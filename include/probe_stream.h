@@ -307,7 +307,7 @@ pv_status probe_update_static(const pv_desc* desc, uint64_t frame, const void* r
  * the selection and packing of every volume in one launch. Results equal
  * those of the same calls made volume by volume. The batch refers to the
  * volumes; they must outlive it and be used only through it while it is in
- * use. All entry points except probe_batch_tune are asynchronous on `stream`
+ * use. All entry points except the two tuners are asynchronous on `stream`
  * and can be captured in a CUDA graph (kernel arguments are fixed at capture).
  *  probe_batch_create   vols[n]; probes_per_item 0 picks np from the probe
  *                       count and the SM count, otherwise np (clamped to what
@@ -324,6 +324,25 @@ pv_status probe_update_static(const pv_desc* desc, uint64_t frame, const void* r
  *                       the volumes' tiles, changed bits, frame counters and
  *                       hysteresis are restored afterwards. Synchronises the
  *                       stream; out_probes_per_item (may be NULL) gets np.
+ *  probe_batch_autotune the batch's plan tuned over probes per item, ray
+ *                       and weight ring depths, TMEM operand stages (F32
+ *                       form) and the CTA count: a coordinate search from the
+ *                       default plan, each candidate timed over `reps` blend
+ *                       launches with these inputs (state restored as for
+ *                       probe_batch_tune), the fastest kept. cache_path (may
+ *                       be NULL: no cache) names a text file of tuned plans,
+ *                       one line per key; the key holds the library build
+ *                       (size and modification time of the loaded library),
+ *                       the device name and SM count, the formats, interiors
+ *                       and every volume's probe count and rays. A key found
+ *                       there is used without timing (out->from_cache = 1);
+ *                       otherwise the result is appended. The file is read and
+ *                       appended without locking: concurrent tuners of one
+ *                       file may both append (the last line of a key wins).
+ *                       Synchronises the stream. out (may be NULL): the plan
+ *                       in use afterwards and the timings. Errors:
+ *                       PV_ERR_INVALID (NULL argument, cache file not
+ *                       writable), PV_ERR_OOM, PV_ERR_CUDA.
  *  probe_batch_info     the batch's current np.
  */
 #define PV_MAX_BATCH 16
@@ -336,6 +355,20 @@ pv_status probe_batch_update(pv_batch* batch, const void* const* radiance, const
 pv_status probe_batch_select_and_pack(pv_batch* batch, pv_frame* out, void* stream);
 pv_status probe_batch_tune(pv_batch* batch, const void* const* radiance, const void* const* dist,
                            const float* const* dirs, int32_t reps, int32_t* out_probes_per_item, void* stream);
+typedef struct pv_tune_result {
+  int32_t probes_per_item;   /* the plan in use after the call */
+  int32_t ray_stages;        /* ray tile ring depth */
+  int32_t weight_stages;     /* weight tile ring depth */
+  int32_t tmem_stages;       /* F32 form: TMEM operand stages (0 otherwise) */
+  int32_t ctas;              /* CTAs of the blend launch */
+  int32_t candidates;        /* plans timed (0 when the cache answered) */
+  int32_t from_cache;        /* 1: the plan came from the cache file */
+  float best_us;             /* blend time of the chosen plan per launch, as tuned */
+  float default_us;          /* blend time of the default plan per launch, as tuned */
+} pv_tune_result;
+pv_status probe_batch_autotune(pv_batch* batch, const void* const* radiance, const void* const* dist,
+                               const float* const* dirs, int32_t reps, const char* cache_path,
+                               pv_tune_result* out, void* stream);
 
 /* ----------------------------------------------------------------- server */
 /*

@@ -54,6 +54,15 @@ class pv_volume_info(C.Structure):
                 ("error_word", C.c_void_p)]
 
 
+class pv_tune_result(C.Structure):
+    _fields_ = [("probes_per_item", C.c_int32), ("ray_stages", C.c_int32), ("weight_stages", C.c_int32),
+                ("tmem_stages", C.c_int32), ("ctas", C.c_int32), ("candidates", C.c_int32),
+                ("from_cache", C.c_int32), ("best_us", C.c_float), ("default_us", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class pv_frame(C.Structure):
     _fields_ = [("color_planes", C.c_void_p), ("vis_planes", C.c_void_p),
                 ("index_c", C.c_void_p), ("index_v", C.c_void_p),
@@ -103,6 +112,8 @@ def _load():
         "probe_batch_update": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]),
         "probe_batch_select_and_pack": (i32, [vp, C.POINTER(pv_frame), vp]),
         "probe_batch_tune": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(i32), vp]),
+        "probe_batch_autotune": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i32, C.c_char_p,
+                                       C.POINTER(pv_tune_result), vp]),
         "pv_server_create": (i32, [C.POINTER(pv_server_desc), C.POINTER(vp)]),
         "pv_server_destroy": (i32, [vp]),
         "pv_server_open": (i32, [vp, i32, C.POINTER(pv_desc)]),
@@ -320,6 +331,15 @@ def probe_batch_tune(batch: int, radiance, dist, dirs, reps: int = 3, stream=Non
     return n.value
 
 
+def probe_batch_autotune(batch: int, radiance, dist, dirs, reps: int = 3, cache_path=None,
+                         stream=None) -> pv_tune_result:
+    r = pv_tune_result()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(lib.probe_batch_autotune(batch, _ptr_array(radiance), _ptr_array(dist), _ptr_array(dirs), int(reps),
+                                    path, C.byref(r), _stream(stream)), "probe_batch_autotune")
+    return r
+
+
 class _DeviceArray:
     """Exposes a device pointer to torch through __cuda_array_interface__ (no copy)."""
 
@@ -442,6 +462,10 @@ class ProbeBatch:
 
     def tune(self, radiance, dist, dirs, reps: int = 3, stream=None) -> int:
         return probe_batch_tune(self.handle, radiance, dist, dirs, reps, stream)
+
+    def autotune(self, radiance, dist, dirs, reps: int = 3, cache_path=None, stream=None) -> dict:
+        """Tune the plan (probes per item, ring depths, TMEM stages, CTAs); see probe_batch_autotune."""
+        return probe_batch_autotune(self.handle, radiance, dist, dirs, reps, cache_path, stream).as_dict()
 
 
 PV_PENDING_STATUS = 1

@@ -1240,7 +1240,9 @@ cudaError_t dev_info(DevInfo* d) {
 // Shared-memory layout for volumes shaped like k, with work items of at most
 // np_want probes (fewer when shared memory demands). Fills every field of tp
 // except items.
-cudaError_t make_layout(const pv_dev& k, int form, int np_want, int smem_max, TcParams& tp, size_t* smem) {
+// lim: optional upper bounds of the ray, weight and TMEM A ring depths (0: none).
+cudaError_t make_layout(const pv_dev& k, int form, int np_want, int smem_max, TcParams& tp, size_t* smem,
+                        const pv_tc_opts* lim = nullptr) {
   const int sb = k.state_fmt == PV_FMT_F16 ? 2 : 4;
   if (k.nc != kNC || k.nv != kNV) return cudaErrorInvalidValue;
   if (k.w_rb != ROWB || k.w_vb != Shp::NVP || k.w_rows != Shp::NVP + Shp::NCP) return cudaErrorInvalidValue;
@@ -1274,13 +1276,16 @@ cudaError_t make_layout(const pv_dev& k, int form, int np_want, int smem_max, Tc
   // split forms' 26 KB, 4 of 13 KB); the ray tiles come from HBM, so the ray
   // ring takes the rest (up to 16 stages) to keep enough bytes in flight.
   int ws = tp.wstage > 16384 ? 3 : 4;
+  if (lim && lim->weight_stages > 0) ws = lim->weight_stages;
   while (ws > 2 && (size_t)ws * tp.wstage + (size_t)3 * tp.xstage > rings) --ws;
   int xs = (int)((rings - (size_t)ws * tp.wstage) / tp.xstage);
   if (xs > 16) xs = 16;
+  if (lim && lim->ray_stages > 0 && xs > lim->ray_stages) xs = lim->ray_stages;
   if (xs < 2) return cudaErrorInvalidConfiguration;
   tp.abase = round_up_c(Shp::CBASE + 2 * Shp::NCP, 32);
   tp.as_ = form == kF32 ? (512 - tp.abase) / 32 : 1;
   if (tp.as_ > 6) tp.as_ = 6;
+  if (form == kF32 && lim && lim->tmem_stages > 0 && tp.as_ > lim->tmem_stages) tp.as_ = lim->tmem_stages;
   if (form == kF32 && tp.as_ < 2) return cudaErrorInvalidConfiguration;
   tp.np = np;
   tp.xs = xs;
@@ -1470,7 +1475,14 @@ cudaError_t pv_launch_blend_tc(pv_volume* v, const void* rad, const void* dist, 
 }
 
 cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc_batch** out) {
-  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  pv_tc_opts o = {};
+  o.probes_per_item = np_want;
+  return pv_tc_batch_create_opts(vols, n, &o, out);
+}
+
+cudaError_t pv_tc_batch_create_opts(pv_volume* const* vols, int n, const pv_tc_opts* opts, pv_tc_batch** out) {
+  if (n < 1 || n > kMaxBatch || !opts) return cudaErrorInvalidValue;
+  const int np_want = opts->probes_per_item;
   cudaError_t e = get_encoder();
   DevInfo di;
   if (e == cudaSuccess) e = dev_info(&di);
@@ -1487,7 +1499,7 @@ cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc
   pv_tc_batch* b = new pv_tc_batch();
   memset(b, 0, sizeof(pv_tc_batch));
   TcParams& tp = b->args.tp;
-  e = make_layout(k0, form, np, di.smem_max, tp, &b->smem);
+  e = make_layout(k0, form, np, di.smem_max, tp, &b->smem, opts);
   if (e == cudaSuccess) {
     int items = 0;
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
@@ -1502,6 +1514,7 @@ cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc
     }
     tp.items = items;
     b->grid = items < di.sms ? items : di.sms;
+    if (opts->ctas > 0 && opts->ctas < b->grid) b->grid = opts->ctas;
     b->args.nvol = n;
     b->form = form;
     b->sb = sb;
@@ -1518,6 +1531,14 @@ cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc
 void pv_tc_batch_destroy(pv_tc_batch* b) { delete b; }
 
 int pv_tc_batch_np(const pv_tc_batch* b) { return b->args.tp.np; }
+
+void pv_tc_batch_config(const pv_tc_batch* b, pv_tc_opts* o) {
+  o->probes_per_item = b->args.tp.np;
+  o->ray_stages = b->args.tp.xs;
+  o->weight_stages = b->args.tp.ws;
+  o->tmem_stages = b->form == kF32 ? b->args.tp.as_ : 0;
+  o->ctas = b->grid;
+}
 
 cudaError_t pv_tc_batch_launch(pv_tc_batch* b, const void* const* rad, const void* const* dist, cudaStream_t st) {
   BlendArgs<kMaxBatch>* a = new BlendArgs<kMaxBatch>(b->args);

@@ -147,7 +147,15 @@ void pv_tc_plan_destroy(pv_volume* v);
 cudaError_t pv_launch_blend_tc(pv_volume* v, const void* rad, const void* dist, cudaStream_t s);
 // one persistent launch over the work items of several volumes of equal shapes
 struct pv_tc_batch;
+// Plan knobs of the batched tensor-core blend (0 = the default choice):
+// probes per work item, ray / weight ring depths (upper bounds; shared
+// memory may give fewer), F32 TMEM A stages, CTAs (at most one per SM).
+struct pv_tc_opts {
+  int probes_per_item, ray_stages, weight_stages, tmem_stages, ctas;
+};
 cudaError_t pv_tc_batch_create(pv_volume* const* vols, int n, int np_want, pv_tc_batch** out);
+cudaError_t pv_tc_batch_create_opts(pv_volume* const* vols, int n, const pv_tc_opts* opts, pv_tc_batch** out);
+void pv_tc_batch_config(const pv_tc_batch* b, pv_tc_opts* out);
 void pv_tc_batch_destroy(pv_tc_batch* b);
 int pv_tc_batch_np(const pv_tc_batch* b);
 cudaError_t pv_tc_batch_launch(pv_tc_batch* b, const void* const* rad, const void* const* dist, cudaStream_t s);

@@ -138,6 +138,62 @@ def test_batch_tune_keeps_state():
     batch.close()
 
 
+@pytest.mark.parametrize("operand_fmt", ["f32", "f16"])
+def test_autotune_caches_its_plan_and_keeps_results(operand_fmt, tmp_path):
+    """The tuner leaves the volumes' state as it found it, writes its plan to the cache file,
+    answers the same shape from the cache without timing, and the tuned plan updates the
+    volumes bit for bit as volume-by-volume calls do."""
+    pv = H.lib()
+    specs = [wl.VolumeSpec(s.nx, s.ny, s.nz, s.rays, state_fmt="f16", operand_fmt=operand_fmt) for s in SMALL]
+    vols = [pv.ProbeVolume(s) for s in specs]
+    alone = [pv.ProbeVolume(s) for s in specs]
+    batch = pv.ProbeBatch(vols)
+    streams = _streams(specs, 5)
+    dev, _ = _inputs(streams, 0)
+    args = ([x[0] for x in dev], [x[1] for x in dev], [x[2] for x in dev])
+    batch.update(*args)
+    for v, (r, d, q) in zip(alone, dev):
+        v.update(r, d, q)
+    torch.cuda.synchronize()
+    before = [H.gpu_state(v) for v in vols]
+    cache = tmp_path / "tune.txt"
+    r1 = batch.autotune(*args, reps=2, cache_path=str(cache))
+    assert r1["from_cache"] == 0 and r1["candidates"] >= 5
+    assert 0.0 < r1["best_us"] <= r1["default_us"]
+    assert batch.probes_per_item == r1["probes_per_item"]
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and "\t" in lines[0]
+    after = [H.gpu_state(v) for v in vols]
+    for b, a in zip(before, after):
+        for x, y in zip(b[:4], a[:4]):
+            np.testing.assert_array_equal(x, y)
+        assert b[4] == a[4]
+    # a second batch of the same shapes takes the plan from the cache
+    vols2 = [pv.ProbeVolume(s) for s in specs]
+    batch2 = pv.ProbeBatch(vols2)
+    r2 = batch2.autotune(*args, reps=2, cache_path=str(cache))
+    assert r2["from_cache"] == 1 and r2["candidates"] == 0
+    for k in ("probes_per_item", "ray_stages", "weight_stages", "tmem_stages", "ctas"):
+        assert r2[k] == r1[k], k
+    assert len(cache.read_text().splitlines()) == 1
+    # the tuned plan: next frames equal volume by volume
+    for f in (1, 2):
+        dev, _ = _inputs(streams, f)
+        batch.update([x[0] for x in dev], [x[1] for x in dev], [x[2] for x in dev])
+        for v, (r, d, q) in zip(alone, dev):
+            v.update(r, d, q)
+        frames = batch.select_and_pack()
+        for va, vb, fb in zip(alone, vols, frames):
+            ga, gb = H.gpu_frame(va, va.select_and_pack()), H.gpu_frame(vb, fb)
+            for key in ga:
+                np.testing.assert_array_equal(np.asarray(ga[key]), np.asarray(gb[key]), err_msg=key)
+            sa, sb = H.gpu_state(va), H.gpu_state(vb)
+            for x, y in zip(sa[:4], sb[:4]):
+                np.testing.assert_array_equal(x, y)
+    batch2.close()
+    batch.close()
+
+
 def test_batch_rejects_mixed_shapes_and_too_many():
     pv = H.lib()
     a = pv.ProbeVolume(wl.VolumeSpec(2, 2, 2, 64, state_fmt="f16"))
