@@ -138,8 +138,6 @@ struct BlendVol {
   CUtensorMap last_v, last_c;            // last-transmitted codes (read)
   CUtensorMap cur_v, cur_c;              // current codes (written)
   pv_dev k;
-  const uint8_t* rad_g;                  // the same rays as plain pointers (L2 prefetch)
-  const uint8_t* dist_g;
   int item0;                             // first work item of the volume in the launch
   int nchunks;                           // ray chunks of kc rays
 };
@@ -282,10 +280,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
-}
-// Contiguous global bytes into L2 (16-byte aligned start and size).
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read() {
@@ -657,6 +651,13 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     mbar_init(&efull[0], 2);                         // one loading thread per visibility channel
     mbar_init(&efull[1], 3);                         // and per colour channel
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // every tensor map of the launch toward the TMA unit, while warp 1
+    // allocates tensor memory
+    for (int v = 0; v < a.nvol; ++v) {
+      const CUtensorMap* m[8] = {&a.v[v].dist, &a.v[v].rad, &a.v[v].st_v, &a.v[v].st_c,
+                                 &a.v[v].last_v, &a.v[v].last_c, &a.v[v].cur_v, &a.v[v].cur_c};
+      for (int i = 0; i < 8; ++i) asm volatile("prefetch.tensormap [%0];" ::"l"(m[i]) : "memory");
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -681,32 +682,11 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     // ahead of the MMAs as the ray ring allows (no wait for the previous
     // kernel). Visibility chunk: d rows into lane quarter 0; colour chunk:
     // R, G, B rows into quarters 1..3.
-    if (elect_one()) {
-      for (int v = 0; v < a.nvol; ++v) {
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].dist) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&a.v[v].rad) : "memory");
-      }
-    }
-    __syncwarp();
     // A stage is free once the converters hold its rays (F32: in TMEM) or
     // once the MMAs that read it completed (16-bit). Tiles land on xfull for
     // the converters, except 16-bit colour tiles, which the MMAs read as they
     // are: those land on the chunk's ready barrier, and this thread adds the
     // four arrivals the converters would have made.
-    // Each item's ray rows are contiguous per channel (the item's probes are
-    // consecutive): they are prefetched into L2 whole, one item ahead, so
-    // that HBM streams full rows while the chunk tiles (64-byte slices of
-    // every row) are read from L2.
-    auto prefetch_item = [&](int item) {
-      const BlendVol& bv = a.v[vol_of(a, item)];
-      const int p0 = (item - bv.item0) * np, npi = min(np, bv.k.P - p0);
-      const size_t rb = (size_t)bv.k.R * (kTmemA ? 4 : 2);
-      const uint32_t bytes = (uint32_t)(npi * rb);
-      prefetch_l2(bv.dist_g + (size_t)p0 * rb, bytes);
-      for (int c = 0; c < 3; ++c) prefetch_l2(bv.rad_g + ((size_t)c * bv.k.P + p0) * rb, bytes);
-    };
-    if (rounds > 0 && elect_one()) prefetch_item(blockIdx.x);
-    __syncwarp();
     int x = 0, n = 0;
     uint32_t ph = 0;
     bool ok = true;
@@ -714,8 +694,6 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
       const int item = blockIdx.x + it * gridDim.x;
       const BlendVol& bv = a.v[vol_of(a, item)];
       const int p0 = (item - bv.item0) * np;
-      if (it + 1 < rounds && elect_one()) prefetch_item(item + gridDim.x);
-      __syncwarp();
       for (int phase = 0; phase < 2 && ok; ++phase) {
         for (int kc = 0; kc < bv.nchunks; ++kc, ++n) {
           if (kTmemA) ok = mbar_wait_warp(&xempty[x], ph ^ 1, err);
@@ -749,32 +727,52 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     // The weight tile images (written by the weights kernel): visibility
     // chunk hi rows then lo rows; colour chunk hi then lo rows adjacent, so
     // that one MMA of N = 2 NCP takes both parts.
-    pv_grid_wait();
+    // Everything the loop reads of the launch parameters for the first item
+    // is fetched before the grid wait: those first reads miss the constant
+    // cache, and after the wait they would delay the first weight tile (and so
+    // the first MMA) by their latency. The empty asm keeps each value in a
+    // register from before the wait.
     const uint32_t wvb = (uint32_t)S::NVP * ROWB, wcb = (uint32_t)S::NCP * ROWB;
+    const int ws_n = tp.ws;
+    const uint32_t wstage = (uint32_t)tp.wstage, tx_wv = tp.tx_wv, tx_wc = tp.tx_wc;
+    auto vol_params = [&](int item, const uint8_t*& w_op, size_t& chunk_b, size_t& plane_b, int& nch) {
+      const BlendVol& bv = a.v[vol_of(a, item)];
+      w_op = (const uint8_t*)bv.k.w_op;
+      chunk_b = (size_t)bv.k.w_rows * ROWB;
+      plane_b = (size_t)bv.k.w_chunks * chunk_b;
+      nch = bv.nchunks;
+    };
+    const uint8_t* w_op0 = nullptr;
+    size_t chunk_b0 = 0, plane_b0 = 0;
+    int nch0 = 0;
+    if (rounds > 0) vol_params(blockIdx.x, w_op0, chunk_b0, plane_b0, nch0);
+    asm volatile("" : "+l"(w_op0), "+l"(chunk_b0), "+l"(plane_b0), "+r"(nch0));
+    asm volatile("" ::"r"(ws_n), "r"(wstage), "r"(tx_wv), "r"(tx_wc));
+    pv_grid_wait();
     // Tiles land on the chunk's ready barrier; a stage is refilled once the
     // MMAs of the chunk that last read it completed.
     int w = 0, n = 0;
     bool ok = true;
     for (int it = 0; it < rounds && ok; ++it) {
-      const int item = blockIdx.x + it * gridDim.x;
-      const BlendVol& bv = a.v[vol_of(a, item)];
-      const size_t chunk_b = (size_t)bv.k.w_rows * ROWB;
-      const size_t plane_b = (size_t)bv.k.w_chunks * chunk_b;
+      const uint8_t* w_op = w_op0;
+      size_t chunk_b = chunk_b0, plane_b = plane_b0;
+      int nchunks = nch0;
+      if (it > 0) vol_params(blockIdx.x + it * gridDim.x, w_op, chunk_b, plane_b, nchunks);
       for (int phase = 0; phase < 2 && ok; ++phase) {
-        for (int kc = 0; kc < bv.nchunks; ++kc, ++n) {
-          ok = wait_done_warp(done, n - tp.ws, err);
+        for (int kc = 0; kc < nchunks; ++kc, ++n) {
+          ok = wait_done_warp(done, n - ws_n, err);
           if (!ok) break;
-          const uint32_t st = smem_u32(wring + (size_t)w * tp.wstage);
-          const uint8_t* src = (const uint8_t*)bv.k.w_op + (size_t)kc * chunk_b + (phase == 0 ? 0 : wvb);
+          const uint32_t st = smem_u32(wring) + (uint32_t)w * wstage;
+          const uint8_t* src = w_op + (size_t)kc * chunk_b + (phase == 0 ? 0 : wvb);
           const uint32_t wb = phase == 0 ? wvb : wcb;
           if (elect_one()) {
             uint64_t* b = &ready[n & (kRing - 1)];
-            mbar_expect_tx(b, phase == 0 ? tp.tx_wv : tp.tx_wc);
+            mbar_expect_tx(b, phase == 0 ? tx_wv : tx_wc);
             bulk_g2s(st, src, wb, b);
             if (kSplitW) bulk_g2s(st + wb, src + plane_b, wb, b);
           }
           __syncwarp();
-          if (++w == tp.ws) w = 0;
+          if (++w == ws_n) w = 0;
         }
       }
     }
@@ -1012,13 +1010,6 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
         tma_load_3d(s_lc, &bv.last_c, 0, p0, chc, &efull[1]);
       }
     };
-    if (io) {
-      for (int v = 0; v < a.nvol; ++v) {
-        const BlendVol& bv = a.v[v];
-        const CUtensorMap* m[6] = {&bv.st_v, &bv.st_c, &bv.last_v, &bv.last_c, &bv.cur_v, &bv.cur_c};
-        for (int i = 0; i < 6; ++i) asm volatile("prefetch.tensormap [%0];" ::"l"(m[i]) : "memory");
-      }
-    }
     pv_grid_wait();
     if (rounds > 0 && io) {
       if (do_v) issue_prefetch(blockIdx.x, true);
@@ -1358,8 +1349,6 @@ cudaError_t encode_ray_maps(const pv_dev& k, int form, const TcParams& tp, const
   const int ob = form == kF32 ? 4 : 2;
   cudaError_t e = encode_2d(&bv.rad, k.operand_fmt, rad, k.R, (uint64_t)3 * k.P, (uint64_t)k.R * ob, tp.kc, tp.np);
   if (e == cudaSuccess) e = encode_2d(&bv.dist, k.operand_fmt, dist, k.R, k.P, (uint64_t)k.R * ob, tp.kc, tp.np);
-  bv.rad_g = (const uint8_t*)rad;
-  bv.dist_g = (const uint8_t*)dist;
   return e;
 }
 
