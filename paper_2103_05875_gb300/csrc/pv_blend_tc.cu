@@ -658,6 +658,17 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
                                  &a.v[v].last_v, &a.v[v].last_c, &a.v[v].cur_v, &a.v[v].cur_c};
       for (int i = 0; i < 8; ++i) asm volatile("prefetch.tensormap [%0];" ::"l"(m[i]) : "memory");
     }
+    // The first item's first ray tiles (all stages are free) go out now, while
+    // warp 1 allocates tensor memory; the ray producer continues after them.
+    if (tp.items > (int)blockIdx.x) {
+      const BlendVol& bv = a.v[vol_of(a, blockIdx.x)];
+      const int p0 = ((int)blockIdx.x - bv.item0) * tp.np;
+      const int pre = min(tp.xs, bv.nchunks);
+      for (int kc = 0; kc < pre; ++kc) {
+        mbar_expect_tx(&xfull[kc], tp.tx_xv);
+        tma_load_2d(smem + tp.off_xr + (size_t)kc * tp.xstage, &bv.dist, kc * tp.kc, p0, &xfull[kc]);
+      }
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -687,15 +698,17 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
     // the converters, except 16-bit colour tiles, which the MMAs read as they
     // are: those land on the chunk's ready barrier, and this thread adds the
     // four arrivals the converters would have made.
-    int x = 0, n = 0;
-    uint32_t ph = 0;
+    // the prologue issued the first item's first `pre` visibility tiles
+    const int pre = rounds > 0 ? min(tp.xs, a.v[vol_of(a, blockIdx.x)].nchunks) : 0;
+    int x = pre == tp.xs ? 0 : pre, n = pre;
+    uint32_t ph = pre == tp.xs ? 1u : 0u;
     bool ok = true;
     for (int it = 0; it < rounds && ok; ++it) {
       const int item = blockIdx.x + it * gridDim.x;
       const BlendVol& bv = a.v[vol_of(a, item)];
       const int p0 = (item - bv.item0) * np;
       for (int phase = 0; phase < 2 && ok; ++phase) {
-        for (int kc = 0; kc < bv.nchunks; ++kc, ++n) {
+        for (int kc = (it == 0 && phase == 0) ? pre : 0; kc < bv.nchunks; ++kc, ++n) {
           if (kTmemA) ok = mbar_wait_warp(&xempty[x], ph ^ 1, err);
           else ok = wait_done_warp(done, n - tp.xs, err);
           if (!ok) break;
