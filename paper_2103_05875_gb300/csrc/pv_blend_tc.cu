@@ -1112,8 +1112,10 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
             if (kv.cur_v) tma_store_3d(&bv.cur_v, 0, p0, chv, s_lv);
             bulk_commit();
           }
-          bulk_wait_read();                         // the boxes may be refilled now
-          if (next < tp.items && ok) issue_prefetch(next, true);
+          if (next < tp.items && ok) {              // the boxes are refilled once the stores read them
+            bulk_wait_read();
+            issue_prefetch(next, true);
+          }
         }
       }
       // ---- colour
@@ -1152,8 +1154,10 @@ __global__ void __launch_bounds__(NT, 1) k_blend_tc(const __grid_constant__ Blen
             if (kv.cur_c) tma_store_3d(&bv.cur_c, 0, p0, chc, s_lc);
             bulk_commit();
           }
-          bulk_wait_read();
-          if (next < tp.items && ok) issue_prefetch(next, false);
+          if (next < tp.items && ok) {
+            bulk_wait_read();
+            issue_prefetch(next, false);
+          }
         }
       }
       eph ^= 1;
