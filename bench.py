@@ -36,7 +36,7 @@ FPG = 4          # frames per captured graph in the timed replays
 # DRAM bytes (read + write) of one k_blend_tc launch of the FP32 form from one ncu capture
 # of this workload, valid only for the kernel source it was taken on: reported as null once
 # the source has changed.
-BLEND_TRAFFIC = {"source_sha256_prefix": "5f5881b82d4e5d54", "f32": 27400960 + 0, "f16": 18617600 + 0}
+BLEND_TRAFFIC = {"source_sha256_prefix": "b9ec67cf29b80880", "f32": 27401472 + 1024, "f16": 18619136 + 0}
 METRIC = "probes updated+packed/sec at 16^3 probes x 256 rays (plain FP32 form)"
 UNIT = "probes/s"
 WORKLOAD = "16x16x16 probes, 256 rays/probe, colour 6x6+1, vis 14x14+1, FP16 state, h=0.97, s=50"
