@@ -120,3 +120,31 @@ def test_client_ignores_ids_and_counts_past_the_volume():
     _check(client, oc, ov)
     client.close()
     vol.close()
+
+
+@pytest.mark.parametrize("nc,nv", [(5, 9), (7, 13), (3, 4)])
+def test_client_odd_interiors_and_ragged_blocks(nc, nv):
+    """Interiors whose colour rows start at odd samples of the planes' 32-bit words and whose
+    visibility rows start anywhere in a 12-byte chunk, on a volume whose block rows (15 slots)
+    split the decode's groups of slots and whose probe count (45) leaves the last group short:
+    full, then partial selections, each equal to the oracle's decode."""
+    pv = H.lib()
+    spec = wl.VolumeSpec(5, 3, 3, 64, hysteresis=0.0, state_fmt="f16", color_interior=nc, vis_interior=nv)
+    vol = pv.ProbeVolume(spec)
+    client = pv.ProbeClient(spec)
+    oc, ov = _oracle_client(spec)
+    fs = wl.FrameStream(spec, 21, mode="stationary", step_frame=1, step_fraction=0.4)
+    counts = []
+    for f in range(3):
+        (r, d, q), _ = H.device_inputs(fs, f)
+        vol.update(r, d, q)
+        fr = vol.select_and_pack(want_host_counts=True)
+        client.apply(fr)
+        g = H.gpu_frame(vol, fr)
+        counts.append(g["count_c"])
+        oc, ov = _oracle_apply(spec, oc, ov, g)
+        torch.cuda.synchronize()
+        _check(client, oc, ov)
+    assert counts[0] == spec.probes and 0 < counts[1] < spec.probes
+    client.close()
+    vol.close()
