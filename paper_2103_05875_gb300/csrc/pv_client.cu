@@ -30,70 +30,65 @@ struct pv_client {
   float* tex_c;      // [3][P][tc*tc] colour values
   uint16_t* tex_v;   // [2][P][tv*tv] visibility texels (binary16 bits)
   uint16_t* src;     // guard-band tables: per colour then visibility tile position, the interior texel it holds
+  int src_voff;      // the visibility table's first entry (a 16-byte boundary)
   int src_q;         // their size in 16-byte words
 };
 
 namespace {
 
-constexpr int CA_THREADS = 256;
-constexpr int CA_SLOTS = 4;                             // slots per block (a power of two, <= 16)
-constexpr int CA_BATCH = 2;                             // 16-byte delta words a thread loads at once
+constexpr int CA_WARPS = 8;
+constexpr int CA_THREADS = 32 * CA_WARPS;
+constexpr int CA_SLOTS = CA_WARPS;                      // slots per block: one per warp
+constexpr int CA_BATCH = 2;                             // 16-byte delta words a thread stages
+constexpr int CA_CB = 4;                                // colour samples a lane loads at once
+constexpr int CA_VB = 3;                                // visibility chunks a lane loads at once
 
 struct CaArgs {
-  int P, nc, nv, tc, tv, bw, cheight, cpitch, vheight, vpitch;
+  int P, nc, nv, tc, tv, bw, crow, vpitch;
+  size_t cplane, vplane;                 // plane sizes: colour in samples, visibility in bytes
   int kind, lsb;
-  uint32_t rcp_nc, rcp_nv, rcp_3, rcp_3nc;
+  uint32_t rcp_nc, rcp_Tc;
   int kv;                                // 12-byte visibility chunks a slot's row can touch
-  uint32_t rcp_kv, rcp_wc;
+  uint32_t rcp_kv;
   int vw_c, vw_v;                        // texels per vector store of a colour / visibility tile
-  uint32_t rcp_cvec, rcp_vvec;           // ceil(2^31 / vectors per tile)
+  uint32_t rcp_cvec;                     // ceil(2^31 / vectors per colour tile channel)
   const uint16_t* planes_c;
   const uint8_t* planes_v;
   const uint16_t* delta_c;
   const uint16_t* delta_v;
   const uint32_t* count_c;
   const uint32_t* count_v;
-  const uint16_t* src;                   // guard-band tables, src_q 16-byte words
-  int src_q;
-  uint32_t off_vv, off_src, off_rawc, off_rawv, off_dq;   // dynamic shared memory layout (CaDyn)
+  const uint16_t* src;                   // guard-band tables, src_q 16-byte words, visibility from src_voff
+  int src_q, src_voff;
+  uint32_t off_src, off_warp, warp_bytes;   // dynamic shared memory layout (CaDyn)
   float* tex_c;
   uint16_t* tex_v;
 };
 
-// 32-bit words holding a row of n colour samples (16-bit) that starts at any
-// sample of a plane row.
-__host__ __device__ constexpr int ca_words_c(int n) { return n / 2 + 1; }
-
-// Shared memory sized to the volume's interiors (dynamic, after CaShared),
-// byte offsets of:
-//   float    vc[CA_SLOTS][3][Tc]     decoded colour interiors of the block's slots
-//   uint32_t vv[CA_SLOTS][Tv]        visibility interiors: R | G << 16
-//   uint16_t src_c[tc*tc], src_v[tv*tv]   per tile position: the interior texel it holds
-//   uint32_t rawc[CA_SLOTS][3][nc][wc]    the plane words of each slot's colour rows
-//   uint32_t rawv[CA_SLOTS][nv][kv][3]    the three plane words of each visibility chunk
+// Dynamic shared memory, byte offsets of:
 //   uint4    dq[CA_BATCH][2][CA_THREADS]  the first 16-byte delta words each thread sums
+//   uint16_t src_c[tc*tc], src_v[tv*tv]   per tile position: the interior texel it holds
+//                                         (src_v on a 16-byte boundary; copied in whole
+//                                         16-byte words)
+//   per warp: float vc[3][Tc], uint32_t vv[Tv]   its slot's decoded colour interior and
+//                                         visibility interior (R | G << 16)
 struct CaDyn {
-  uint32_t vc, vv, src_c, src_v, rawc, rawv, dq, bytes;
+  uint32_t src, warp, warp_bytes, bytes;
 };
 
-__host__ __device__ inline CaDyn ca_dyn_layout(int nc, int nv, int tc, int tv, int kv) {
+inline CaDyn ca_dyn_layout(int nc, int nv, int src_q) {
   const auto up16 = [](uint32_t x) { return (x + 15u) & ~15u; };
   CaDyn L;
-  L.vc = 0;
-  L.vv = up16(L.vc + CA_SLOTS * 3 * nc * nc * 4);
-  L.src_c = up16(L.vv + CA_SLOTS * nv * nv * 4);
-  L.src_v = L.src_c + tc * tc * 2;
-  L.rawc = up16(L.src_v + tv * tv * 2);
-  L.rawv = up16(L.rawc + CA_SLOTS * 3 * nc * ca_words_c(nc) * 4);
-  L.dq = up16(L.rawv + CA_SLOTS * nv * kv * 3 * 4);
-  // (the tables are copied in whole 16-byte words: room up to rawc)
-  L.bytes = L.dq + CA_BATCH * 2 * CA_THREADS * 16;
+  L.src = CA_BATCH * 2 * CA_THREADS * 16;
+  L.warp = L.src + src_q * 16;
+  L.warp_bytes = up16((3 * nc * nc + nv * nv) * 4);
+  L.bytes = L.warp + CA_WARPS * L.warp_bytes;
   return L;
 }
 
 struct CaShared {
   int id_c[CA_SLOTS], id_v[CA_SLOTS];    // probe of each slot, -1 for none
-  uint32_t red[2 * CA_THREADS / 32];
+  uint32_t red[2 * CA_WARPS];
 };
 
 // Adds the eight 16-bit deltas of a 16-byte word to acc (each dp2a adds both
@@ -105,112 +100,107 @@ __device__ __forceinline__ uint32_t sum16(uint32_t acc, uint4 v) {
   return a0 + a1;
 }
 
-// Whole tiles of the block's slots, VW texels per store: vector v of channel
-// c of slot s holds tile texels VW*v .. VW*v+VW-1, each the interior texel
-// src[e] of the slot's staged values (`get`).
-template <int VW, typename V, typename T, typename G>
-__device__ __forceinline__ void store_tiles(T* tex, int P, int tt, int nch, int ns, const int* ids,
-                                            const uint16_t* src, uint32_t rcp_nvec, G get) {
-  const int nvec = tt / VW;
-  for (int it = threadIdx.x; it < ns * nch * nvec; it += CA_THREADS) {
-    const int t = pv::fdiv(it, rcp_nvec), v = it - t * nvec;
-    const int s = t / nch, c = t - s * nch;
-    const int p = ids[s];
-    if (p < 0) continue;
-    union {
-      V vec;
-      T el[VW];
-    } u;
-#pragma unroll
-    for (int q = 0; q < VW; ++q) u.el[q] = get(s, c, src[VW * v + q]);
-    *reinterpret_cast<V*>(tex + ((size_t)c * P + p) * tt + VW * v) = u.vec;
-  }
-}
-
 __device__ __forceinline__ float color_value(uint32_t code, int kind) {
   if (kind == PV_CODE_UNORM10) return (float)code / 1023.0f;     // correctly rounded
   return __half2float(__ushort_as_half((unsigned short)(code << 5)));   // UF10 is binary16's top bits
 }
 
-// 4- and 16-byte asynchronous copies global -> shared (both addresses aligned
-// to the size), and the wait for every copy the thread issued.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
-}
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned),
+// and the wait for every copy the thread issued.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-__global__ void __launch_bounds__(CA_THREADS, 8) k_client_apply(const CaArgs a) {
+// VW consecutive table entries (VW * 2 bytes, aligned to that size).
+template <int VW>
+__device__ __forceinline__ void load_src(const uint16_t* src, int e, uint16_t (&out)[VW]) {
+  if constexpr (VW == 8) {
+    const uint4 q = *reinterpret_cast<const uint4*>(src + e);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      out[2 * k] = (uint16_t)(w[k] & 0xFFFFu);
+      out[2 * k + 1] = (uint16_t)(w[k] >> 16);
+    }
+  } else if constexpr (VW == 4) {
+    const uint2 q = *reinterpret_cast<const uint2*>(src + e);
+    out[0] = (uint16_t)(q.x & 0xFFFFu);
+    out[1] = (uint16_t)(q.x >> 16);
+    out[2] = (uint16_t)(q.y & 0xFFFFu);
+    out[3] = (uint16_t)(q.y >> 16);
+  } else {
+#pragma unroll
+    for (int k = 0; k < VW; ++k) out[k] = src[e + k];
+  }
+}
+
+// The colour tiles of probe p (three channels), VW texels per store, by the
+// warp: vector v of channel c holds tile texels VW*q .. VW*q+VW-1.
+template <int VW, typename V>
+__device__ __forceinline__ void store_color(float* tex, int P, int p, int tt, const uint16_t* src, const float* vc,
+                                            int T, uint32_t rcp_nvec, int lane) {
+  const int nvec = tt / VW;
+  for (int v = lane; v < 3 * nvec; v += 32) {
+    const int c = pv::fdiv(v, rcp_nvec), q = v - c * nvec;
+    uint16_t e[VW];
+    load_src<VW>(src, VW * q, e);
+    union {
+      V vec;
+      float el[VW];
+    } u;
+#pragma unroll
+    for (int k = 0; k < VW; ++k) u.el[k] = vc[c * T + e[k]];
+    *reinterpret_cast<V*>(tex + ((size_t)c * P + p) * tt + VW * q) = u.vec;
+  }
+}
+
+// The visibility tiles of probe p (R and G from the same interior word), VW
+// texels per store, by the warp.
+template <int VW, typename V>
+__device__ __forceinline__ void store_vis(uint16_t* tex, int P, int p, int tt, const uint16_t* src,
+                                          const uint32_t* vv, int lane) {
+  const int nvec = tt / VW;
+  for (int v = lane; v < nvec; v += 32) {
+    uint16_t e[VW];
+    load_src<VW>(src, VW * v, e);
+    union {
+      V vec;
+      uint16_t el[VW];
+    } r, g;
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {
+      const uint32_t w = vv[e[k]];
+      r.el[k] = (uint16_t)(w & 0xFFFFu);
+      g.el[k] = (uint16_t)(w >> 16);
+    }
+    *reinterpret_cast<V*>(tex + (size_t)p * tt + VW * v) = r.vec;
+    *reinterpret_cast<V*>(tex + ((size_t)P + p) * tt + VW * v) = g.vec;
+  }
+}
+
+__global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   __shared__ __align__(16) CaShared sh;
   extern __shared__ __align__(16) uint8_t ca_dyn[];
-  const int n_c = a.nc, n_v = a.nv, Tc = n_c * n_c, Tv = n_v * n_v;
-  float* vc = reinterpret_cast<float*>(ca_dyn);
-  uint32_t* vv = reinterpret_cast<uint32_t*>(ca_dyn + a.off_vv);
-  uint16_t* src_c = reinterpret_cast<uint16_t*>(ca_dyn + a.off_src);
-  uint16_t* src_v = src_c + a.tc * a.tc;
-  uint32_t* rawc = reinterpret_cast<uint32_t*>(ca_dyn + a.off_rawc);
-  uint32_t* rawv = reinterpret_cast<uint32_t*>(ca_dyn + a.off_rawv);
-  uint4* dq = reinterpret_cast<uint4*>(ca_dyn + a.off_dq);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n_c = a.nc, n_v = a.nv, Tc = n_c * n_c;
+  uint4* dq = reinterpret_cast<uint4*>(ca_dyn);
+  uint16_t* src_c = reinterpret_cast<uint16_t*>(ca_dyn + a.off_src);
+  uint16_t* src_v = src_c + a.src_voff;
+  float* vc = reinterpret_cast<float*>(ca_dyn + a.off_warp + wid * a.warp_bytes);
+  uint32_t* vv = reinterpret_cast<uint32_t*>(vc + 3 * Tc);
   const int k0 = blockIdx.x * CA_SLOTS;
   const int nsl = min(CA_SLOTS, a.P - k0);             // the block's slots inside the volume
-  // block of the update texture of the block's first slot; slot s follows
-  const int by0 = k0 / a.bw, bx0 = k0 - by0 * a.bw;
-  const auto slot_block = [&](int s, int& bx, int& by) {
-    bx = bx0 + s;
-    by = by0;
-    while (bx >= a.bw) {
-      bx -= a.bw;
-      ++by;
-    }
-  };
+  const int slot = k0 + wid;                           // the warp's slot
+  const int by = slot / a.bw, bx = slot - by * a.bw;  // its block of the update textures
 
-  // ---- loads, all issued before any is used. Slots past the frame's counts
-  // are read too (they lie inside the planes) and dropped below.
+  // ---- block-wide loads: counts, tables and the deltas before the block's
+  // first slot (in 16-byte words, the first CA_BATCH of each thread staged in
+  // dq where only that thread reads them, and a tail), and the block's own
+  // deltas (first warp: lanes 0..SLOTS-1 colour, then visibility)
   const uint32_t cnt_c_raw = *a.count_c, cnt_v_raw = *a.count_v;
   for (int q = tid; q < a.src_q; q += CA_THREADS) cp_async16(src_c + 8 * q, a.src + 8 * q);
-  // colour: the 32-bit words holding row i of slot s in plane c, items
-  // (s, c, i, k) with k fastest, copied to rawc[((s*3 + c)*n + i)*wc + k]
-  const int wc = ca_words_c(n_c), items_c = CA_SLOTS * 3 * n_c * wc;
-  const size_t cplane = (size_t)a.cheight * a.cpitch;
-  for (int it = tid; it < items_c; it += CA_THREADS) {
-    const int t = pv::fdiv(it, a.rcp_wc), k = it - t * wc;
-    const int u = pv::fdiv(t, a.rcp_nc), i = t - u * n_c;
-    const int s = pv::fdiv(u, a.rcp_3), c = u - s * 3;
-    if (s >= nsl) continue;
-    int bx, by;
-    slot_block(s, bx, by);
-    const int w0 = (bx * n_c) >> 1, w = w0 + k;
-    if (w > ((bx * n_c + n_c - 1) >> 1)) continue;
-    cp_async4(rawc + it, reinterpret_cast<const uint8_t*>(a.planes_c) + c * cplane +
-                             (size_t)(by * n_c + i) * a.cpitch + 4 * (size_t)w);
-  }
-  // visibility: chunk k of row i of slot s, the atlas row's stream bytes
-  // 12w..12w+11 (texels 3w..3w+2), which are the words at column 4w of the
-  // three planes; items (s, i, k), copied to rawv[3*it + plane]
-  const int items_v = CA_SLOTS * n_v * a.kv;
-  const size_t vplane = (size_t)a.vheight * a.vpitch;
-  for (int it = tid; it < items_v; it += CA_THREADS) {
-    const int t = pv::fdiv(it, a.rcp_kv), k = it - t * a.kv;
-    const int s = pv::fdiv(t, a.rcp_nv), i = t - s * n_v;
-    if (s >= nsl) continue;
-    int bx, by;
-    slot_block(s, bx, by);
-    const int xs = n_v * bx, w = xs / 3 + k;
-    if (w > (4 * (xs + n_v) - 1) / 12) continue;
-    const uint8_t* row = a.planes_v + (size_t)(by * n_v + i) * a.vpitch + 4 * (size_t)w;
-    cp_async4(rawv + 3 * it, row);
-    cp_async4(rawv + 3 * it + 1, row + vplane);
-    cp_async4(rawv + 3 * it + 2, row + 2 * vplane);
-  }
-  // deltas: the k0 before the block's first slot in 16-byte words (the first
-  // CA_BATCH of each thread staged in dq, where only that thread reads them)
-  // and a tail, and the block's own (first warp: lanes 0..SLOTS-1 colour, then
-  // visibility)
   const int nq = k0 >> 3;
   const uint4* dc4 = reinterpret_cast<const uint4*>(a.delta_c);
   const uint4* dv4 = reinterpret_cast<const uint4*>(a.delta_v);
@@ -230,6 +220,68 @@ __global__ void __launch_bounds__(CA_THREADS, 8) k_client_apply(const CaArgs a) 
   if (tid < 2 * CA_SLOTS) {
     const int s = tid & (CA_SLOTS - 1);
     if (s < nsl) d = tid >= CA_SLOTS ? a.delta_v[k0 + s] : a.delta_c[k0 + s];
+  }
+
+  // ---- the warp's slot (inside the volume; past the frame's counts it is
+  // decoded and dropped): its colour samples and visibility chunks, loaded
+  // CA_CB / CA_VB per lane at once, decoded into the warp's shared memory
+  if (wid < nsl) {
+    // colour: sample it = (c*n + i)*n + j of the slot, which is its place in vc
+    const uint16_t* pc = a.planes_c + (size_t)by * n_c * a.crow + (size_t)bx * n_c;
+    for (int b0 = 0; b0 < 3 * Tc; b0 += 32 * CA_CB) {
+      uint32_t smp[CA_CB];
+#pragma unroll
+      for (int u = 0; u < CA_CB; ++u) {
+        const int it = b0 + lane + 32 * u;
+        smp[u] = 0;
+        if (it < 3 * Tc) {
+          const int c = pv::fdiv(it, a.rcp_Tc), r = it - c * Tc;
+          const int i = pv::fdiv(r, a.rcp_nc), j = r - i * n_c;
+          smp[u] = pc[c * a.cplane + (size_t)i * a.crow + j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CA_CB; ++u) {
+        const int it = b0 + lane + 32 * u;
+        if (it < 3 * Tc) vc[it] = color_value(a.lsb ? (smp[u] & 0x3FFu) : (smp[u] >> 6), a.kind);
+      }
+    }
+    // visibility: chunk k of row i, the atlas row's stream bytes 12w..12w+11
+    // (texels 3w..3w+2, w = w0 + k), which are the words at column 4w of the
+    // three planes; stream byte 12w + b sits in plane b % 3, byte b / 3 of
+    // that word. Texels outside the slot's row are dropped.
+    const int xs = n_v * bx, w0 = xs / 3, nk = (4 * (xs + n_v) - 1) / 12 - w0 + 1;
+    const uint8_t* pw = a.planes_v + (size_t)by * n_v * a.vpitch + 4 * (size_t)w0;
+    for (int b0 = 0; b0 < n_v * a.kv; b0 += 32 * CA_VB) {
+      uint32_t wv[CA_VB][3];
+#pragma unroll
+      for (int u = 0; u < CA_VB; ++u) {
+        const int it = b0 + lane + 32 * u;
+        const int i = pv::fdiv(it, a.rcp_kv), k = it - i * a.kv;
+        wv[u][0] = wv[u][1] = wv[u][2] = 0;
+        if (it < n_v * a.kv && k < nk) {
+          const uint32_t* w = reinterpret_cast<const uint32_t*>(pw + (size_t)i * a.vpitch + 4 * k);
+          wv[u][0] = w[0];
+          wv[u][1] = w[a.vplane / 4];
+          wv[u][2] = w[a.vplane / 2];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CA_VB; ++u) {
+        const int it = b0 + lane + 32 * u;
+        const int i = pv::fdiv(it, a.rcp_kv), k = it - i * a.kv;
+        if (it < n_v * a.kv && k < nk) {
+          const uint32_t p0 = wv[u][0], p1 = wv[u][1], p2 = wv[u][2];
+          const uint32_t t3[3] = {__byte_perm(__byte_perm(p0, p1, 0x1040), p2, 0x3410),
+                                  __byte_perm(__byte_perm(p1, p2, 0x2051), p0, 0x3610),
+                                  __byte_perm(__byte_perm(p2, p0, 0x3072), p1, 0x3710)};
+          const int x = 3 * (w0 + k) - xs;             // texel 3w relative to the slot's first
+#pragma unroll
+          for (int e = 0; e < 3; ++e)
+            if (x + e >= 0 && x + e < n_v) vv[i * n_v + x + e] = t3[e];
+        }
+      }
+    }
   }
 
   // ---- delta sums modulo 2^16, one partial per warp
@@ -259,12 +311,13 @@ __global__ void __launch_bounds__(CA_THREADS, 8) k_client_apply(const CaArgs a) 
   // ---- probe ids: the deltas before the block's slots plus the inclusive
   // prefix of its own (the sums before k0 are of this frame's deltas whenever
   // the block has a slot below the count)
-  if (tid < 32) {
+  if (wid == 0) {
     const int s = lane & (CA_SLOTS - 1);
     const bool vis = lane >= CA_SLOTS;
     const int ns = vis ? ns_v : ns_c;
     uint32_t base_c = 0, base_v = 0;
-    for (int w = 0; w < CA_THREADS / 32; ++w) {
+#pragma unroll
+    for (int w = 0; w < CA_WARPS; ++w) {
       base_c += sh.red[2 * w];
       base_v += sh.red[2 * w + 1];
     }
@@ -280,56 +333,22 @@ __global__ void __launch_bounds__(CA_THREADS, 8) k_client_apply(const CaArgs a) 
       else sh.id_c[s] = p;
     }
   }
-  // ---- interiors from the staged words: colour items (s, c, i, j)
-  for (int it = tid; it < ns_c * 3 * Tc; it += CA_THREADS) {
-    const int t = pv::fdiv(it, a.rcp_nc), j = it - t * n_c;     // t = (s*3 + c)*n + i
-    const int s = pv::fdiv(t, a.rcp_3nc);
-    int bx, by;
-    slot_block(s, bx, by);
-    const int o = ((bx * n_c) & 1) + j;                         // sample o of the row's first word
-    const uint32_t word = rawc[t * wc + (o >> 1)];
-    const uint32_t sample = (o & 1) ? word >> 16 : word & 0xFFFFu;
-    const uint32_t code = a.lsb ? (sample & 0x3FFu) : (sample >> 6);
-    vc[t * n_c + j] = color_value(code, a.kind);
-  }
-  // visibility chunks (s, i, k): stream byte 12w + b sits in plane b % 3, byte
-  // b / 3 of that word; keep the texels inside the slot's row
-  for (int it = tid; it < ns_v * n_v * a.kv; it += CA_THREADS) {
-    const int t = pv::fdiv(it, a.rcp_kv), k = it - t * a.kv;    // t = s*n + i
-    const int s = pv::fdiv(t, a.rcp_nv);
-    int bx, by;
-    slot_block(s, bx, by);
-    const int xs = n_v * bx, x = 3 * (xs / 3 + k) - xs;         // texel 3w relative to the slot's first
-    if (x >= n_v) continue;
-    const uint32_t p0 = rawv[3 * it], p1 = rawv[3 * it + 1], p2 = rawv[3 * it + 2];
-    const uint32_t t3[3] = {__byte_perm(__byte_perm(p0, p1, 0x1040), p2, 0x3410),
-                            __byte_perm(__byte_perm(p1, p2, 0x2051), p0, 0x3610),
-                            __byte_perm(__byte_perm(p2, p0, 0x3072), p1, 0x3710)};
-#pragma unroll
-    for (int e = 0; e < 3; ++e)
-      if (x + e >= 0 && x + e < n_v) vv[t * n_v + x + e] = t3[e];
-  }
   __syncthreads();
 
-  // whole tiles: interior and guard band, vector stores along each tile
-  {
-    const int T = a.nc * a.nc;
-    const auto get = [&](int s, int c, int e) { return vc[(s * 3 + c) * T + e]; };
+  // ---- the warp's tiles: interior and guard band, vector stores along each tile
+  const int p_c = sh.id_c[wid], p_v = sh.id_v[wid];
+  if (p_c >= 0) {
     const int tt = a.tc * a.tc;
-    if (a.vw_c == 4) store_tiles<4, float4>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, src_c, a.rcp_cvec, get);
-    else if (a.vw_c == 2) store_tiles<2, float2>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, src_c, a.rcp_cvec, get);
-    else store_tiles<1, float>(a.tex_c, a.P, tt, 3, ns_c, sh.id_c, src_c, a.rcp_cvec, get);
+    if (a.vw_c == 4) store_color<4, float4>(a.tex_c, a.P, p_c, tt, src_c, vc, Tc, a.rcp_cvec, lane);
+    else if (a.vw_c == 2) store_color<2, float2>(a.tex_c, a.P, p_c, tt, src_c, vc, Tc, a.rcp_cvec, lane);
+    else store_color<1, float>(a.tex_c, a.P, p_c, tt, src_c, vc, Tc, a.rcp_cvec, lane);
   }
-  {
-    const auto get = [&](int s, int c, int e) {
-      const uint32_t v = vv[s * Tv + e];
-      return (uint16_t)(c ? v >> 16 : v & 0xFFFFu);
-    };
+  if (p_v >= 0) {
     const int tt = a.tv * a.tv;
-    if (a.vw_v == 8) store_tiles<8, uint4>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, src_v, a.rcp_vvec, get);
-    else if (a.vw_v == 4) store_tiles<4, uint2>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, src_v, a.rcp_vvec, get);
-    else if (a.vw_v == 2) store_tiles<2, uint32_t>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, src_v, a.rcp_vvec, get);
-    else store_tiles<1, uint16_t>(a.tex_v, a.P, tt, 2, ns_v, sh.id_v, src_v, a.rcp_vvec, get);
+    if (a.vw_v == 8) store_vis<8, uint4>(a.tex_v, a.P, p_v, tt, src_v, vv, lane);
+    else if (a.vw_v == 4) store_vis<4, uint2>(a.tex_v, a.P, p_v, tt, src_v, vv, lane);
+    else if (a.vw_v == 2) store_vis<2, uint32_t>(a.tex_v, a.P, p_v, tt, src_v, vv, lane);
+    else store_vis<1, uint16_t>(a.tex_v, a.P, p_v, tt, src_v, vv, lane);
   }
 }
 
@@ -352,15 +371,17 @@ pv_status pv_client_create(const pv_desc* d, pv_client** out) {
   cudaGetDevice(&c->device);
   const size_t bc = (size_t)3 * g.P * g.tc * g.tc * sizeof(float), bv = (size_t)2 * g.P * g.tv * g.tv * 2;
   // the guard-band rule of the two tile sizes as tables: tile position -> interior texel
-  const int ntab = g.tc * g.tc + g.tv * g.tv;
-  c->src_q = (ntab * 2 + 15) / 16;
+  // (the visibility table from the first 16-byte boundary after the colour table)
+  c->src_voff = (g.tc * g.tc + 7) / 8 * 8;
+  c->src_q = (c->src_voff + g.tv * g.tv + 7) / 8;
   std::vector<uint16_t> tab((size_t)c->src_q * 8, 0);
-  for (int e = 0; e < ntab; ++e) {
-    const bool vis = e >= g.tc * g.tc;
-    const int t = vis ? g.tv : g.tc, n = vis ? g.nv : g.nc, q = vis ? e - g.tc * g.tc : e;
-    int sr, sc;
-    pv::border_source(q / t, q % t, n, &sr, &sc);
-    tab[e] = (uint16_t)((sr - 1) * n + (sc - 1));
+  for (int vis = 0; vis < 2; ++vis) {
+    const int t = vis ? g.tv : g.tc, n = vis ? g.nv : g.nc;
+    for (int q = 0; q < t * t; ++q) {
+      int sr, sc;
+      pv::border_source(q / t, q % t, n, &sr, &sc);
+      tab[(vis ? c->src_voff : 0) + q] = (uint16_t)((sr - 1) * n + (sc - 1));
+    }
   }
   cudaError_t e = cudaMalloc((void**)&c->tex_c, bc);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->tex_v, bv);
@@ -416,26 +437,22 @@ pv_status pv_client_apply(pv_client* c, const pv_frame* f, void* stream) {
   a.tc = g.tc;
   a.tv = g.tv;
   a.bw = g.bw;
-  a.cheight = g.cheight;
-  a.cpitch = g.cpitch;
-  a.vheight = g.vheight;
+  a.crow = g.cpitch / 2;
   a.vpitch = g.vpitch;
+  a.cplane = (size_t)g.cheight * a.crow;
+  a.vplane = (size_t)g.vheight * g.vpitch;
   a.kind = c->d.color_code;
   a.lsb = c->d.color_lsb ? 1 : 0;
   a.rcp_nc = pv_rcp31((uint32_t)g.nc);
-  a.rcp_nv = pv_rcp31((uint32_t)g.nv);
+  a.rcp_Tc = pv_rcp31((uint32_t)(g.nc * g.nc));
   // a slot's row spans 4 nv stream bytes, which touch at most this many 12-byte chunks
   a.kv = (4 * g.nv - 1 + 11) / 12 + 1;
   a.rcp_kv = pv_rcp31((uint32_t)a.kv);
-  a.rcp_wc = pv_rcp31((uint32_t)ca_words_c(g.nc));
-  a.rcp_3 = pv_rcp31(3u);
-  a.rcp_3nc = pv_rcp31(3u * (uint32_t)g.nc);
   // widest vector store that divides a tile (the textures are 16-byte aligned)
   const int ttc = g.tc * g.tc, ttv = g.tv * g.tv;
   a.vw_c = ttc % 4 == 0 ? 4 : (ttc % 2 == 0 ? 2 : 1);
   a.vw_v = ttv % 8 == 0 ? 8 : (ttv % 4 == 0 ? 4 : (ttv % 2 == 0 ? 2 : 1));
   a.rcp_cvec = pv_rcp31((uint32_t)(ttc / a.vw_c));
-  a.rcp_vvec = pv_rcp31((uint32_t)(ttv / a.vw_v));
   a.planes_c = f->color_planes;
   a.planes_v = f->vis_planes;
   a.delta_c = f->delta_c;
@@ -446,12 +463,11 @@ pv_status pv_client_apply(pv_client* c, const pv_frame* f, void* stream) {
   a.tex_v = c->tex_v;
   a.src = c->src;
   a.src_q = c->src_q;
-  const CaDyn L = ca_dyn_layout(g.nc, g.nv, g.tc, g.tv, a.kv);
-  a.off_vv = L.vv;
-  a.off_src = L.src_c;
-  a.off_rawc = L.rawc;
-  a.off_rawv = L.rawv;
-  a.off_dq = L.dq;
+  a.src_voff = c->src_voff;
+  const CaDyn L = ca_dyn_layout(g.nc, g.nv, c->src_q);
+  a.off_src = L.src;
+  a.off_warp = L.warp;
+  a.warp_bytes = L.warp_bytes;
   pv_host::DeviceGuard guard(c->device);
   const int blocks = (g.P + CA_SLOTS - 1) / CA_SLOTS;
   k_client_apply<<<blocks, CA_THREADS, L.bytes, reinterpret_cast<cudaStream_t>(stream)>>>(a);
