@@ -37,6 +37,9 @@ FPG = 4          # frames per captured graph in the timed replays
 # of this workload, valid only for the kernel source it was taken on: reported as null once
 # the source has changed.
 BLEND_TRAFFIC = {"source_sha256_prefix": "b9ec67cf29b80880", "f32": 27401472 + 1024, "f16": 18619136 + 0}
+# The same capture's tensor-pipe share (sm__pipe_tensor_cycles_active, percent of the launch's
+# cycles): the kernel against its other roofline, keyed to the same source.
+BLEND_TENSOR_PIPE = {"source_sha256_prefix": "b9ec67cf29b80880", "f32": 0.219, "f16": 0.070}
 METRIC = "probes updated+packed/sec at 16^3 probes x 256 rays (plain FP32 form)"
 UNIT = "probes/s"
 WORKLOAD = "16x16x16 probes, 256 rays/probe, colour 6x6+1, vis 14x14+1, FP16 state, h=0.97, s=50"
@@ -985,6 +988,7 @@ def run_ours(args, ws, rank, local):
     src = os.path.join(ROOT, "paper_2103_05875_gb300", "csrc", "pv_blend_tc.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     traffic = BLEND_TRAFFIC.get(forms[0]) if sha == BLEND_TRAFFIC["source_sha256_prefix"] else None
+    tensor = BLEND_TENSOR_PIPE.get(forms[0]) if sha == BLEND_TENSOR_PIPE["source_sha256_prefix"] else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -1000,7 +1004,10 @@ def run_ours(args, ws, rank, local):
                               "the chained step overlaps them (programmatic dependent launch)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "k_blend_tc",
-                     "launch_us": blend_ms * 1e3, "peak_source": peak_src, "algorithmic_bytes_per_launch": alg},
+                     "launch_us": blend_ms * 1e3, "peak_source": peak_src, "algorithmic_bytes_per_launch": alg,
+                     "tensor_pipe_active": tensor,
+                     "tensor_pipe_note": "ncu sm__pipe_tensor_cycles_active of one launch of the same source "
+                                         "(null once the source has changed)"},
         "clocks": clk,
     }
     forms_out = {}
