@@ -8,14 +8,16 @@
 // of the codes (UF10 or UNORM10) in binary32; visibility texels are the
 // transmitted binary16 bits.
 //
-// One kernel: a block owns SLOTS consecutive slots of both textures. It sums
-// the deltas before its slots itself (no grid-wide scan), unpacks its slots'
-// interiors into shared memory, then writes their whole tiles with coalesced
-// stores. Each thread issues all of its global loads (counts, plane samples,
-// deltas) before it uses any of them, so a block waits for memory once; slots
-// past the frame's counts are read too (they lie inside the planes) and
-// dropped. Probe ids at or past P and counts past P are ignored, so a damaged
-// frame cannot make the kernel write outside the textures.
+// One kernel: a block owns SLOTS consecutive slots of both textures, one warp
+// per slot. The block stages the guard-band tables (built once per client)
+// and the deltas before its first slot with asynchronous copies and sums the
+// deltas itself (no grid-wide scan); meanwhile each warp reads its slot's
+// colour samples and visibility chunks in one batch and decodes them into its
+// own shared memory. After the ids are known, each warp writes its slot's
+// whole tiles with vector stores. Slots past the frame's counts are decoded
+// too (they lie inside the planes) and dropped. Probe ids at or past P and
+// counts past P are ignored, so a damaged frame cannot make the kernel write
+// outside the textures.
 #include <string.h>
 
 #include <vector>
