@@ -15,7 +15,8 @@
 // colour samples and visibility chunks in one batch and decodes them into its
 // own shared memory. After the ids are known, each warp writes its slot's
 // whole tiles with vector stores. Slots past the frame's counts are decoded
-// too (they lie inside the planes) and dropped. Probe ids at or past P and
+// too (they lie inside the planes) and dropped; deltas are read only below the
+// counts. Probe ids at or past P and
 // counts past P are ignored, so a damaged frame cannot make the kernel write
 // outside the textures.
 #include <string.h>
@@ -197,92 +198,115 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   const int slot = k0 + wid;                           // the warp's slot
   const int by = slot / a.bw, bx = slot - by * a.bw;  // its block of the update textures
 
-  // ---- block-wide loads: counts, tables and the deltas before the block's
-  // first slot (in 16-byte words, the first CA_BATCH of each thread staged in
-  // dq where only that thread reads them, and a tail), and the block's own
-  // deltas (first warp: lanes 0..SLOTS-1 colour, then visibility)
-  const uint32_t cnt_c_raw = *a.count_c, cnt_v_raw = *a.count_v;
+  // ---- the warp's slot (inside the volume; past the frame's counts it is
+  // decoded and dropped): its colour samples and visibility chunks, CA_CB /
+  // CA_VB per lane at once; the first batch of each is loaded before anything
+  // waits, then decoded into the warp's shared memory
+  const bool live = wid < nsl;
+  // colour: sample it = (c*n + i)*n + j of the slot, which is its place in vc
+  const uint16_t* pc = a.planes_c + (size_t)by * n_c * a.crow + (size_t)bx * n_c;
+  const auto load_c = [&](int b0, uint32_t(&smp)[CA_CB]) {
+#pragma unroll
+    for (int u = 0; u < CA_CB; ++u) {
+      const int it = b0 + lane + 32 * u;
+      smp[u] = 0;
+      if (it < 3 * Tc) {
+        const int c = pv::fdiv(it, a.rcp_Tc), r = it - c * Tc;
+        const int i = pv::fdiv(r, a.rcp_nc), j = r - i * n_c;
+        smp[u] = pc[c * a.cplane + (size_t)i * a.crow + j];
+      }
+    }
+  };
+  const auto put_c = [&](int b0, const uint32_t(&smp)[CA_CB]) {
+#pragma unroll
+    for (int u = 0; u < CA_CB; ++u) {
+      const int it = b0 + lane + 32 * u;
+      if (it < 3 * Tc) vc[it] = color_value(a.lsb ? (smp[u] & 0x3FFu) : (smp[u] >> 6), a.kind);
+    }
+  };
+  // visibility: chunk k of row i, the atlas row's stream bytes 12w..12w+11
+  // (texels 3w..3w+2, w = w0 + k), which are the words at column 4w of the
+  // three planes; stream byte 12w + b sits in plane b % 3, byte b / 3 of that
+  // word. Texels outside the slot's row are dropped.
+  const int xs = n_v * bx, w0 = xs / 3, nk = (4 * (xs + n_v) - 1) / 12 - w0 + 1;
+  const uint8_t* pw = a.planes_v + (size_t)by * n_v * a.vpitch + 4 * (size_t)w0;
+  const auto load_v = [&](int b0, uint32_t(&wv)[CA_VB][3]) {
+#pragma unroll
+    for (int u = 0; u < CA_VB; ++u) {
+      const int it = b0 + lane + 32 * u;
+      const int i = pv::fdiv(it, a.rcp_kv), k = it - i * a.kv;
+      wv[u][0] = wv[u][1] = wv[u][2] = 0;
+      if (it < n_v * a.kv && k < nk) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(pw + (size_t)i * a.vpitch + 4 * k);
+        wv[u][0] = w[0];
+        wv[u][1] = w[a.vplane / 4];
+        wv[u][2] = w[a.vplane / 2];
+      }
+    }
+  };
+  const auto put_v = [&](int b0, const uint32_t(&wv)[CA_VB][3]) {
+#pragma unroll
+    for (int u = 0; u < CA_VB; ++u) {
+      const int it = b0 + lane + 32 * u;
+      const int i = pv::fdiv(it, a.rcp_kv), k = it - i * a.kv;
+      if (it < n_v * a.kv && k < nk) {
+        const uint32_t p0 = wv[u][0], p1 = wv[u][1], p2 = wv[u][2];
+        const uint32_t t3[3] = {__byte_perm(__byte_perm(p0, p1, 0x1040), p2, 0x3410),
+                                __byte_perm(__byte_perm(p1, p2, 0x2051), p0, 0x3610),
+                                __byte_perm(__byte_perm(p2, p0, 0x3072), p1, 0x3710)};
+        const int x = 3 * (w0 + k) - xs;               // texel 3w relative to the slot's first
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+          if (x + e >= 0 && x + e < n_v) vv[i * n_v + x + e] = t3[e];
+      }
+    }
+  };
+  uint32_t smp[CA_CB], wv[CA_VB][3];
+  if (live) {
+    load_c(0, smp);
+    load_v(0, wv);
+  }
+
+  // ---- block-wide: the tables, the counts, then only the deltas the frame
+  // holds: those before the block's first slot when that slot is below the
+  // count (in 16-byte words, the first CA_BATCH of each thread staged in dq,
+  // where only that thread reads them, and a tail) and the block's own below
+  // the count (first warp: lanes 0..SLOTS-1 colour, then visibility)
   for (int q = tid; q < a.src_q; q += CA_THREADS) cp_async16(src_c + 8 * q, a.src + 8 * q);
-  const int nq = k0 >> 3;
+  const int cnt_c = (int)min(*a.count_c, (uint32_t)a.P), cnt_v = (int)min(*a.count_v, (uint32_t)a.P);
+  const int ns_c = max(0, min(nsl, cnt_c - k0)), ns_v = max(0, min(nsl, cnt_v - k0));
+  const int na_c = ns_c > 0 ? k0 : 0, na_v = ns_v > 0 ? k0 : 0;
+  const int nq_c = na_c >> 3, nq_v = na_v >> 3;
   const uint4* dc4 = reinterpret_cast<const uint4*>(a.delta_c);
   const uint4* dv4 = reinterpret_cast<const uint4*>(a.delta_v);
 #pragma unroll
   for (int u = 0; u < CA_BATCH; ++u) {
     const int q = tid + u * CA_THREADS;
-    if (q < nq) {
-      cp_async16(dq + (2 * u) * CA_THREADS + tid, dc4 + q);
-      cp_async16(dq + (2 * u + 1) * CA_THREADS + tid, dv4 + q);
-    }
+    if (q < nq_c) cp_async16(dq + (2 * u) * CA_THREADS + tid, dc4 + q);
+    if (q < nq_v) cp_async16(dq + (2 * u + 1) * CA_THREADS + tid, dv4 + q);
   }
   uint32_t sum_c = 0, sum_v = 0, d = 0;
-  if (tid < (k0 & 7)) {
-    sum_c = a.delta_c[8 * nq + tid];
-    sum_v = a.delta_v[8 * nq + tid];
-  }
+  if (tid < (na_c & 7)) sum_c = a.delta_c[8 * nq_c + tid];
+  if (tid < (na_v & 7)) sum_v = a.delta_v[8 * nq_v + tid];
   if (tid < 2 * CA_SLOTS) {
     const int s = tid & (CA_SLOTS - 1);
-    if (s < nsl) d = tid >= CA_SLOTS ? a.delta_v[k0 + s] : a.delta_c[k0 + s];
+    const bool vis = tid >= CA_SLOTS;
+    if (s < (vis ? ns_v : ns_c)) d = vis ? a.delta_v[k0 + s] : a.delta_c[k0 + s];
   }
 
-  // ---- the warp's slot (inside the volume; past the frame's counts it is
-  // decoded and dropped): its colour samples and visibility chunks, loaded
-  // CA_CB / CA_VB per lane at once, decoded into the warp's shared memory
-  if (wid < nsl) {
-    // colour: sample it = (c*n + i)*n + j of the slot, which is its place in vc
-    const uint16_t* pc = a.planes_c + (size_t)by * n_c * a.crow + (size_t)bx * n_c;
-    for (int b0 = 0; b0 < 3 * Tc; b0 += 32 * CA_CB) {
-      uint32_t smp[CA_CB];
-#pragma unroll
-      for (int u = 0; u < CA_CB; ++u) {
-        const int it = b0 + lane + 32 * u;
-        smp[u] = 0;
-        if (it < 3 * Tc) {
-          const int c = pv::fdiv(it, a.rcp_Tc), r = it - c * Tc;
-          const int i = pv::fdiv(r, a.rcp_nc), j = r - i * n_c;
-          smp[u] = pc[c * a.cplane + (size_t)i * a.crow + j];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < CA_CB; ++u) {
-        const int it = b0 + lane + 32 * u;
-        if (it < 3 * Tc) vc[it] = color_value(a.lsb ? (smp[u] & 0x3FFu) : (smp[u] >> 6), a.kind);
-      }
+  // ---- decode: the first batches, then any further ones one at a time
+  if (live) {
+    put_c(0, smp);
+    for (int b0 = 32 * CA_CB; b0 < 3 * Tc; b0 += 32 * CA_CB) {
+      uint32_t t[CA_CB];
+      load_c(b0, t);
+      put_c(b0, t);
     }
-    // visibility: chunk k of row i, the atlas row's stream bytes 12w..12w+11
-    // (texels 3w..3w+2, w = w0 + k), which are the words at column 4w of the
-    // three planes; stream byte 12w + b sits in plane b % 3, byte b / 3 of
-    // that word. Texels outside the slot's row are dropped.
-    const int xs = n_v * bx, w0 = xs / 3, nk = (4 * (xs + n_v) - 1) / 12 - w0 + 1;
-    const uint8_t* pw = a.planes_v + (size_t)by * n_v * a.vpitch + 4 * (size_t)w0;
-    for (int b0 = 0; b0 < n_v * a.kv; b0 += 32 * CA_VB) {
-      uint32_t wv[CA_VB][3];
-#pragma unroll
-      for (int u = 0; u < CA_VB; ++u) {
-        const int it = b0 + lane + 32 * u;
-        const int i = pv::fdiv(it, a.rcp_kv), k = it - i * a.kv;
-        wv[u][0] = wv[u][1] = wv[u][2] = 0;
-        if (it < n_v * a.kv && k < nk) {
-          const uint32_t* w = reinterpret_cast<const uint32_t*>(pw + (size_t)i * a.vpitch + 4 * k);
-          wv[u][0] = w[0];
-          wv[u][1] = w[a.vplane / 4];
-          wv[u][2] = w[a.vplane / 2];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < CA_VB; ++u) {
-        const int it = b0 + lane + 32 * u;
-        const int i = pv::fdiv(it, a.rcp_kv), k = it - i * a.kv;
-        if (it < n_v * a.kv && k < nk) {
-          const uint32_t p0 = wv[u][0], p1 = wv[u][1], p2 = wv[u][2];
-          const uint32_t t3[3] = {__byte_perm(__byte_perm(p0, p1, 0x1040), p2, 0x3410),
-                                  __byte_perm(__byte_perm(p1, p2, 0x2051), p0, 0x3610),
-                                  __byte_perm(__byte_perm(p2, p0, 0x3072), p1, 0x3710)};
-          const int x = 3 * (w0 + k) - xs;             // texel 3w relative to the slot's first
-#pragma unroll
-          for (int e = 0; e < 3; ++e)
-            if (x + e >= 0 && x + e < n_v) vv[i * n_v + x + e] = t3[e];
-        }
-      }
+    put_v(0, wv);
+    for (int b0 = 32 * CA_VB; b0 < n_v * a.kv; b0 += 32 * CA_VB) {
+      uint32_t t[CA_VB][3];
+      load_v(b0, t);
+      put_v(b0, t);
     }
   }
 
@@ -290,19 +314,14 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   cp_async_wait_all();
 #pragma unroll
   for (int u = 0; u < CA_BATCH; ++u) {
-    if (tid + u * CA_THREADS < nq) {
-      sum_c = sum16(sum_c, dq[(2 * u) * CA_THREADS + tid]);
-      sum_v = sum16(sum_v, dq[(2 * u + 1) * CA_THREADS + tid]);
-    }
+    const int q = tid + u * CA_THREADS;
+    if (q < nq_c) sum_c = sum16(sum_c, dq[(2 * u) * CA_THREADS + tid]);
+    if (q < nq_v) sum_v = sum16(sum_v, dq[(2 * u + 1) * CA_THREADS + tid]);
   }
-  for (int q = tid + CA_BATCH * CA_THREADS; q < nq; q += CA_THREADS) {
-    sum_c = sum16(sum_c, dc4[q]);
-    sum_v = sum16(sum_v, dv4[q]);
-  }
+  for (int q = tid + CA_BATCH * CA_THREADS; q < nq_c; q += CA_THREADS) sum_c = sum16(sum_c, dc4[q]);
+  for (int q = tid + CA_BATCH * CA_THREADS; q < nq_v; q += CA_THREADS) sum_v = sum16(sum_v, dv4[q]);
   sum_c = __reduce_add_sync(0xffffffffu, sum_c);
   sum_v = __reduce_add_sync(0xffffffffu, sum_v);
-  const int cnt_c = (int)min(cnt_c_raw, (uint32_t)a.P), cnt_v = (int)min(cnt_v_raw, (uint32_t)a.P);
-  const int ns_c = max(0, min(nsl, cnt_c - k0)), ns_v = max(0, min(nsl, cnt_v - k0));
   if (ns_c == 0 && ns_v == 0) return;                   // uniform: the block has no slot in the frame
   if (lane == 0) {
     sh.red[2 * wid] = sum_c;
@@ -311,8 +330,7 @@ __global__ void __launch_bounds__(CA_THREADS) k_client_apply(const CaArgs a) {
   __syncthreads();
 
   // ---- probe ids: the deltas before the block's slots plus the inclusive
-  // prefix of its own (the sums before k0 are of this frame's deltas whenever
-  // the block has a slot below the count)
+  // prefix of its own
   if (wid == 0) {
     const int s = lane & (CA_SLOTS - 1);
     const bool vis = lane >= CA_SLOTS;
