@@ -403,7 +403,13 @@ pv_status pv_client_create(const pv_desc* d, pv_client** out) {
       tab[(vis ? c->src_voff : 0) + q] = (uint16_t)((sr - 1) * n + (sc - 1));
     }
   }
-  cudaError_t e = cudaMalloc((void**)&c->tex_c, bc);
+  // the decode's shared memory can pass the 48 KB a launch gets by default
+  // (up to about 50 KB for 16x16 interiors): raise the kernel's limit to it
+  const uint32_t dyn = ca_dyn_layout(g.nc, g.nv, c->src_q).bytes;
+  cudaError_t e = dyn > 48u * 1024u
+                      ? cudaFuncSetAttribute(k_client_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)
+                      : cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->tex_c, bc);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->tex_v, bv);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->src, tab.size() * 2);
   if (e == cudaSuccess) e = cudaMemcpy(c->src, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice);

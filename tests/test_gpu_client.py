@@ -122,12 +122,13 @@ def test_client_ignores_ids_and_counts_past_the_volume():
     vol.close()
 
 
-@pytest.mark.parametrize("nc,nv", [(5, 9), (7, 13), (3, 4)])
+@pytest.mark.parametrize("nc,nv", [(5, 9), (7, 13), (3, 4), (16, 16)])
 def test_client_odd_interiors_and_ragged_blocks(nc, nv):
     """Interiors whose colour rows start at odd samples of the planes' 32-bit words and whose
-    visibility rows start anywhere in a 12-byte chunk, on a volume whose block rows (15 slots)
-    split the decode's groups of slots and whose probe count (45) leaves the last group short:
-    full, then partial selections, each equal to the oracle's decode."""
+    visibility rows start anywhere in a 12-byte chunk, and the largest interiors (16x16, whose
+    decode needs more than the default 48 KB of shared memory), on a volume whose block rows
+    (15 slots) split the decode's groups of slots and whose probe count (45) leaves the last
+    group short: full, then partial selections, each equal to the oracle's decode."""
     pv = H.lib()
     spec = wl.VolumeSpec(5, 3, 3, 64, hysteresis=0.0, state_fmt="f16", color_interior=nc, vis_interior=nv)
     vol = pv.ProbeVolume(spec)
